@@ -1,0 +1,309 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself -- dense brute force, special products with a known answer, stencil
+closed forms, the associativity invariant, finite differences.  No GPU.
+
+Each pin is chosen so that a plausible slip in the oracle fails it: a dropped
+product or wrong index (brute force, closed forms), a transposed operand
+(non-square brute force), a sign error (Laplacian closed form), unsorted or
+repeated output columns (structure checks), a lost pattern entry on
+cancellation (explicit-zero test).
+"""
+import numpy as np
+import pytest
+
+from paper_2112_10037_gb300 import gen
+
+pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
+
+
+def _dense(m):
+    return gen.to_dense(m)
+
+
+def _pattern(m):
+    d = np.zeros((m.nrows, m.ncols), bool)
+    rows = np.repeat(np.arange(m.nrows), np.diff(np.asarray(m.row_ptr, np.int64)))
+    d[rows, m.col_idx] = True
+    return d
+
+
+def _assert_sorted_unique(C):
+    rp = np.asarray(C.row_ptr, np.int64)
+    for i in range(C.nrows):
+        seg = C.col_idx[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(seg) > 0), f"row {i} not strictly ascending"
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("shape,density,seed", [
+    ((1, 1, 1), 1.0, 0), ((7, 5, 9), 0.4, 1), ((33, 17, 40), 0.2, 2),
+    ((64, 64, 64), 0.1, 3), ((20, 64, 3), 0.3, 4), ((50, 1, 50), 0.5, 5),
+])
+def test_brute_force_integer_exact(oracle_mod, shape, density, seed):
+    """Integer-valued inputs: every partial sum is an exact integer, so the
+    oracle must equal the dense product bit for bit (Sec. 2.2 definition)."""
+    m, k, n = shape
+    A = gen.random_csr(m, k, density, seed, values="int", empty_rows=0.2)
+    B = gen.random_csr(k, n, density, seed + 100, values="int", empty_rows=0.2)
+    C = oracle_mod.spgemm(A, B)
+    _assert_sorted_unique(C)
+    dense = _dense(A) @ _dense(B)
+    struct = (_pattern(A).astype(np.int64) @ _pattern(B).astype(np.int64)) > 0
+    assert np.array_equal(_pattern(C), struct)
+    assert np.array_equal(_dense(C), np.where(struct, dense, 0.0))
+    assert np.array_equal(np.asarray(C.row_ptr, np.int64), oracle_mod.spgemm_rowptr(A, B))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_brute_force_real_values(oracle_mod, seed):
+    A = gen.random_csr(40, 30, 0.25, seed, values="normal", empty_rows=0.1)
+    B = gen.random_csr(30, 50, 0.25, seed + 7, values="normal", empty_rows=0.1)
+    C = oracle_mod.spgemm(A, B)
+    ref = _dense(A) @ _dense(B)
+    scale = np.abs(_dense(A)) @ np.abs(_dense(B))
+    got = _dense(C)
+    assert np.all(np.abs(got - ref) <= 1e-14 * scale + 1e-300)
+
+
+def test_non_square_operand_order(oracle_mod):
+    """A (3x2) * B (2x4): swapping the operands or transposing one cannot
+    even produce a 3x4 result, and the values are asymmetric."""
+    A = gen.from_dense(np.array([[1.0, 2.0], [0.0, 3.0], [4.0, 0.0]]))
+    B = gen.from_dense(np.array([[1.0, 0.0, 5.0, 0.0], [0.0, 6.0, 7.0, 1.0]]))
+    C = oracle_mod.spgemm(A, B)
+    assert (C.nrows, C.ncols) == (3, 4)
+    expect = np.array([[1.0, 12.0, 19.0, 2.0], [0.0, 18.0, 21.0, 3.0], [4.0, 0.0, 20.0, 0.0]])
+    assert np.array_equal(_dense(C), expect)
+    assert list(np.diff(C.row_ptr)) == [4, 3, 2]
+
+
+def test_cancellation_keeps_structure(oracle_mod):
+    """Products that cancel to 0.0 stay in the pattern (structural C)."""
+    A = gen.from_dense(np.array([[1.0, 1.0]]))
+    B = gen.from_dense(np.array([[2.0, 3.0], [-2.0, 1.0]]))
+    C = oracle_mod.spgemm(A, B)
+    assert list(C.col_idx) == [0, 1]
+    assert C.vals[0] == 0.0 and C.vals[1] == 4.0
+
+
+def test_empty_shapes(oracle_mod):
+    for (m, k, n) in [(0, 0, 0), (0, 5, 3), (4, 0, 3), (4, 5, 0), (3, 3, 3)]:
+        A = gen.random_csr(m, k, 0.5, 1)
+        B = gen.random_csr(k, n, 0.5, 2)
+        if (m, k, n) == (3, 3, 3):
+            A = gen.CSR(3, 3, np.zeros(4, np.int32), np.zeros(0, np.int32), np.zeros(0))
+        C = oracle_mod.spgemm(A, B)
+        assert C.nrows == m and C.ncols == n and C.nnz == 0
+
+
+# ------------------------------------------------------- special products
+def test_identity_products(oracle_mod):
+    A = gen.random_csr(57, 43, 0.2, 11)
+    I_l, I_r = gen.identity(57), gen.identity(43)
+    for C in (oracle_mod.spgemm(I_l, A), oracle_mod.spgemm(A, I_r)):
+        assert np.array_equal(C.row_ptr, A.row_ptr.astype(np.int64))
+        assert np.array_equal(C.col_idx, A.col_idx)
+        assert np.array_equal(C.vals, A.vals)
+
+
+def test_permutation_products(oracle_mod):
+    rng = np.random.default_rng(5)
+    A = gen.random_csr(30, 30, 0.2, 12)
+    perm = rng.permutation(30)
+    P = gen.permutation(perm)
+    # P*A: row i of the result is row perm[i] of A.
+    C = oracle_mod.spgemm(P, A)
+    assert np.array_equal(_dense(C), _dense(A)[perm, :])
+    _assert_sorted_unique(C)
+    # A*P: column perm[c] of A moves to column c (entries re-sorted).
+    C2 = oracle_mod.spgemm(A, P)
+    # (A*P)[:, c] = A[:, i] with perm[i] = c, i.e. A[:, argsort(perm)].
+    assert np.array_equal(_dense(C2), _dense(A)[:, np.argsort(perm)])
+    _assert_sorted_unique(C2)
+
+
+def test_power_of_two_diagonal_scaling(oracle_mod):
+    A = gen.random_csr(25, 25, 0.3, 13)
+    d = 2.0 ** np.random.default_rng(1).integers(-4, 5, 25)
+    C = oracle_mod.spgemm(gen.diagonal(d), A)
+    rows = np.repeat(np.arange(25), np.diff(A.row_ptr))
+    assert np.array_equal(C.vals, A.vals * d[rows])
+    assert np.array_equal(C.col_idx, A.col_idx)
+
+
+# ---------------------------------------------------------- closed forms
+def _lap2d_square_expected(nx):
+    """Closed form of (2D 5-point Laplacian)^2 on an nx x nx grid: 16 + deg(i)
+    on the diagonal, -8 at distance 1, 2 at the four diagonal neighbours, 1
+    at axial distance 2 (all restricted to the grid)."""
+    exp = {}
+    for y in range(nx):
+        for x in range(nx):
+            i = y * nx + x
+            deg = (x > 0) + (x < nx - 1) + (y > 0) + (y < nx - 1)
+            for dy in range(-2, 3):
+                for dx in range(-2, 3):
+                    if abs(dx) + abs(dy) > 2:
+                        continue
+                    xx, yy = x + dx, y + dy
+                    if not (0 <= xx < nx and 0 <= yy < nx):
+                        continue
+                    j = yy * nx + xx
+                    if dx == 0 and dy == 0:
+                        v = 16.0 + deg
+                    elif abs(dx) + abs(dy) == 1:
+                        v = -8.0
+                    elif abs(dx) == 1 and abs(dy) == 1:
+                        v = 2.0
+                    else:
+                        v = 1.0
+                    exp[(i, j)] = v
+    return exp
+
+
+@pytest.mark.parametrize("nx", [1, 2, 3, 8, 64])
+def test_laplacian2d_squared_closed_form(oracle_mod, nx):
+    A = gen.laplacian_2d(nx)
+    C = oracle_mod.spgemm(A, A)
+    _assert_sorted_unique(C)
+    exp = _lap2d_square_expected(nx)
+    assert C.nnz == len(exp)
+    rows = np.repeat(np.arange(C.nrows), np.diff(C.row_ptr))
+    got = {(int(r), int(c)): float(v) for r, c, v in zip(rows, C.col_idx, C.vals)}
+    assert got == exp
+    if nx == 64:
+        # nnz = sum over the 13 offsets of (64-|dx|)(64-|dy|) = 51,972
+        offs = [(dx, dy) for dx in range(-2, 3) for dy in range(-2, 3) if abs(dx) + abs(dy) <= 2]
+        assert C.nnz == sum((64 - abs(dx)) * (64 - abs(dy)) for dx, dy in offs) == 51972
+        interior = 20 * 64 + 20
+        assert got[(interior, interior)] == 20.0
+
+
+@pytest.mark.parametrize("n", [2, 4, 8])
+def test_galerkin_coarse_operator_closed_form(oracle_mod, n):
+    """P^T (A P) for the 3D 7-point operator (6 / -1) and 2x2x2 aggregation
+    is the coarse 7-point operator with 24 on the diagonal and -4 to each
+    face-neighbour aggregate (4 fine edges cross each aggregate face; the
+    12 edges inside an aggregate cancel 24 of the 8*6 = 48)."""
+    A = gen.laplacian_3d(n)
+    P = gen.aggregation_3d(n)
+    R = oracle_mod.transpose(P)
+    AP = oracle_mod.spgemm(A, P)
+    Ac = oracle_mod.spgemm(R, AP)
+    nc = n // 2
+    ref = gen.laplacian_3d(nc)
+    assert np.array_equal(np.asarray(Ac.row_ptr, np.int64), ref.row_ptr.astype(np.int64))
+    assert np.array_equal(Ac.col_idx, ref.col_idx)
+    assert np.array_equal(Ac.vals, np.where(ref.vals == 6.0, 24.0, -4.0))
+
+
+def test_galerkin_full_size_counts(oracle_mod):
+    """nnz(A P) and nnz(P^T A P) at the 96^3 workload (7-point stencil on
+    the 48^3 coarse grid: 7*48^3 - 6*48^2 entries)."""
+    A = gen.laplacian_3d(96)
+    P = gen.aggregation_3d(96)
+    AP_rp = oracle_mod.spgemm_rowptr(A, P)
+    assert AP_rp[-1] == 3_483_648
+    assert 7 * 48 ** 3 - 6 * 48 ** 2 == 760_320
+
+
+def test_laplacian3d_squared_diagonal(oracle_mod):
+    A = gen.laplacian_3d(6)
+    C = oracle_mod.spgemm(A, A)
+    d = _dense(C)
+    deg = np.diff(A.row_ptr) - 1
+    assert np.array_equal(np.diag(d), 36.0 + deg)
+
+
+# ------------------------------------------------------------- invariant
+@pytest.mark.parametrize("seed", [0, 1])
+def test_associativity_invariant(oracle_mod, seed):
+    A = gen.random_csr(300, 200, 0.03, seed)
+    B = gen.random_csr(200, 250, 0.03, seed + 1)
+    x = np.random.default_rng(seed).standard_normal(250)
+    C = oracle_mod.spgemm(A, B)
+    lhs = oracle_mod.spmv(C, x)
+    rhs = oracle_mod.spmv(A, oracle_mod.spmv(B, x))
+    scale = np.abs(_dense(A)) @ (np.abs(_dense(B)) @ np.abs(x))
+    assert np.all(np.abs(lhs - rhs) <= 1e-13 * scale + 1e-300)
+
+
+def test_spmv_and_transpose_vs_dense(oracle_mod):
+    A = gen.random_csr(37, 23, 0.2, 3)
+    x = np.arange(23, dtype=np.float64) - 5
+    assert np.allclose(oracle_mod.spmv(A, x), _dense(A) @ x, rtol=1e-14, atol=1e-14)
+    T = oracle_mod.transpose(A)
+    assert np.array_equal(_dense(T), _dense(A).T)
+    _assert_sorted_unique(T)
+    TT = oracle_mod.transpose(T)
+    assert np.array_equal(TT.col_idx, A.col_idx) and np.array_equal(TT.vals, A.vals)
+
+
+def test_row_products(oracle_mod):
+    A = gen.random_csr(40, 30, 0.2, 4)
+    B = gen.random_csr(30, 60, 0.2, 5)
+    lens = np.diff(B.row_ptr).astype(np.int64)
+    expect = np.array([lens[A.col_idx[A.row_ptr[i]:A.row_ptr[i + 1]]].sum() for i in range(40)])
+    assert np.array_equal(oracle_mod.row_products(A, B), expect)
+
+
+def test_rmat_generator_counts():
+    """Workload recipe check (input side only): R-MAT scale 10 is
+    deterministic and self-loop free, with hubs at low ids."""
+    A = gen.rmat(10, 16).check()
+    rows = np.repeat(np.arange(A.nrows), np.diff(A.row_ptr))
+    assert not np.any(rows == A.col_idx)
+    lens = np.diff(A.row_ptr)
+    assert lens[0] == lens.max()
+    B = gen.rmat(10, 16)
+    assert np.array_equal(A.col_idx, B.col_idx) and np.array_equal(A.vals, B.vals)
+
+
+# -------------------------------------------------------------- gradient
+def _loss(oracle_mod, A, B, W_of):
+    C = oracle_mod.spgemm(A, B)
+    return float(np.sum(W_of(C) * C.vals))
+
+
+def test_backward_vs_dense(oracle_mod):
+    A = gen.random_csr(30, 25, 0.2, 21)
+    B = gen.random_csr(25, 35, 0.2, 22)
+    C = oracle_mod.spgemm(A, B)
+    W = np.random.default_rng(3).standard_normal(C.nnz)
+    da, db = oracle_mod.backward(A, B, C.row_ptr, C.col_idx, W)
+    Wd = _dense(gen.CSR(C.nrows, C.ncols, C.row_ptr.astype(np.int32), C.col_idx, W))
+    dA_dense = Wd @ _dense(B).T
+    dB_dense = _dense(A).T @ Wd
+    ra = np.repeat(np.arange(A.nrows), np.diff(A.row_ptr))
+    rb = np.repeat(np.arange(B.nrows), np.diff(B.row_ptr))
+    assert np.allclose(da, dA_dense[ra, A.col_idx], rtol=1e-13, atol=1e-13)
+    assert np.allclose(db, dB_dense[rb, B.col_idx], rtol=1e-13, atol=1e-13)
+
+
+def test_backward_finite_differences(oracle_mod):
+    """L = sum W*C is bilinear in (A, B), so a one-sided difference
+    (L(A + h e_p) - L(A)) / h equals dA[p] up to rounding, for any h."""
+    A = gen.random_csr(20, 15, 0.3, 31)
+    B = gen.random_csr(15, 18, 0.3, 32)
+    C = oracle_mod.spgemm(A, B)
+    W = np.random.default_rng(4).standard_normal(C.nnz)
+    key = {(int(r), int(c)): t for t, (r, c) in enumerate(
+        zip(np.repeat(np.arange(C.nrows), np.diff(C.row_ptr)), C.col_idx))}
+
+    def W_of(Cn):
+        rows = np.repeat(np.arange(Cn.nrows), np.diff(Cn.row_ptr))
+        return np.array([W[key[(int(r), int(c))]] for r, c in zip(rows, Cn.col_idx)])
+
+    da, db = oracle_mod.backward(A, B, C.row_ptr, C.col_idx, W)
+    L0 = _loss(oracle_mod, A, B, W_of)
+    h = 1e-3
+    for p in range(0, A.nnz, max(1, A.nnz // 12)):
+        A2 = gen.CSR(A.nrows, A.ncols, A.row_ptr, A.col_idx, A.vals.copy())
+        A2.vals[p] += h
+        fd = (_loss(oracle_mod, A2, B, W_of) - L0) / h
+        assert abs(fd - da[p]) <= 1e-9 * (1 + abs(da[p]))
+    for q in range(0, B.nnz, max(1, B.nnz // 12)):
+        B2 = gen.CSR(B.nrows, B.ncols, B.row_ptr, B.col_idx, B.vals.copy())
+        B2.vals[q] += h
+        fd = (_loss(oracle_mod, A, B2, W_of) - L0) / h
+        assert abs(fd - db[q]) <= 1e-9 * (1 + abs(db[q]))
