@@ -1,0 +1,431 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Gustavson SpGEMM hot path.
+
+One step = one whole product C = A*B through the C ABI with the inputs
+resident in HBM: analyse (row product counts, binning), symbolic (row sizes,
+prefix scan, one host sync for nnz(C)), numeric (columns and values).  The
+default workload is C = A*A for the R-MAT power-law adjacency of scale 18,
+edge factor 16, (a,b,c,d) = (0.57, 0.19, 0.19, 0.05), values U(0.5, 1.5),
+FP64, int32 indices.
+
+Metric: GFLOP/s = 2 * (intermediate products) / time.  The JSON line also
+carries the numeric kernel's HBM roofline fraction (algorithmic bytes of
+A, the B rows touched and C written, over its CUDA-event duration), an
+end-to-end figure with host buffers (H2D of A, D2H of C inside the timed
+region), SM clocks sampled during the timed region, and the CPU oracle's
+throughput on a bounded row sample.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--workload rmat|lap2d|stencil3d]
+For N > 1 (torchrun), rank r multiplies a row block of A balanced by product
+count; the blocks are independent, there is no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+from paper_2112_10037_gb300 import gen  # noqa: E402
+
+L2_BYTES = 129 * 1024 * 1024
+PEAKS_FILE = os.path.join(HERE, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ------------------------------------------------------------------ inputs
+def make_workload(name: str):
+    """(A, B, description) on the host; B is A for the square workloads."""
+    if name == "rmat":
+        A = gen.rmat(18, 16)
+        return A, A, {"workload": "rmat_s18_ef16_AxA", "matrix": "R-MAT scale 18, edge factor 16, "
+                      "(0.57,0.19,0.19,0.05), self-loops dropped, duplicates merged, U(0.5,1.5) values",
+                      "rows": A.nrows, "nnz_A": A.nnz}
+    if name == "lap2d":
+        A = gen.laplacian_2d(64)
+        return A, A, {"workload": "laplacian2d_64_AxA", "rows": A.nrows, "nnz_A": A.nnz}
+    if name == "stencil3d":
+        A = gen.laplacian_3d(96)
+        return A, A, {"workload": "laplacian3d_96_AxA", "rows": A.nrows, "nnz_A": A.nnz}
+    raise SystemExit("unknown workload %s" % name)
+
+
+def row_products(A, B):
+    """Per-row product counts from the input structure (host bookkeeping for
+    the byte model and the row sample; the device computes its own)."""
+    lens = np.diff(B.row_ptr.astype(np.int64))
+    per_nz = lens[A.col_idx]
+    cs = np.concatenate([[0], np.cumsum(per_nz)])
+    rp = A.row_ptr.astype(np.int64)
+    return cs[rp[1:]] - cs[rp[:-1]]
+
+
+def balanced_row_blocks(prod, nparts):
+    """Row boundaries splitting the rows into nparts blocks of about equal
+    product count."""
+    cs = np.concatenate([[0], np.cumsum(prod)])
+    targets = cs[-1] * np.arange(1, nparts) / nparts
+    cuts = np.searchsorted(cs, targets)
+    return [0] + [int(c) for c in cuts] + [len(prod)]
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons (read only)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "0x1", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_hbm_peak():
+    try:
+        with open(PEAKS_FILE) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# --------------------------------------------------------- CPU baseline
+def cpu_oracle_leg(A, B, prod, target_seconds=12.0):
+    """The oracle (single-threaded C) on a bounded sample of rows: every
+    s-th row of A, s chosen from a short calibration run so the sample takes
+    about target_seconds.  Returns the cpu_baseline dict."""
+    import oracle
+    oracle.build()
+    total = int(prod.sum())
+    # calibration on a small strided sample
+    s0 = max(1, int(total / 2e7))
+    rows = np.arange(0, A.nrows, s0)
+    t0 = time.perf_counter()
+    oracle.spgemm(oracle.select_rows(A, rows), B)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    rate = max(int(prod[rows].sum()), 1) / dt
+    want = rate * target_seconds
+    stride = max(1, int(round(total / max(want, 1.0))))
+    rows = np.arange(0, A.nrows, stride)
+    sub = oracle.select_rows(A, rows)
+    p = int(prod[rows].sum())
+    t0 = time.perf_counter()
+    oracle.spgemm(sub, B)
+    dt = time.perf_counter() - t0
+    return {"value": 2.0 * p / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": "rows i = 0 mod %d of A (%d rows, %d products, %.1f s single-threaded)"
+                      % (stride, len(rows), p, dt)}
+
+
+# ------------------------------------------------------------ our step
+def run_ours(args, rank, world, A, B, desc):
+    import torch
+    from paper_2112_10037_gb300 import api, build as bld, _native as nat
+
+    bld.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    prod = row_products(A, B)
+    blocks = balanced_row_blocks(prod, world)
+    rb, re = blocks[rank], blocks[rank + 1]
+    my_products = int(prod[rb:re].sum())
+    dA = api.DeviceCSR.from_host(A, device=dev)
+    dB = dA if B is A else api.DeviceCSR.from_host(B, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+
+    kw = {} if world == 1 else {"row_range": (rb, re)}
+
+    def step(profile=False):
+        plan = api.Plan(dA, dB, dtype=torch.float64, **kw)
+        if profile:
+            nat.spgemm_plan_set_profiling(plan.handle, True)
+        rp, nnz = plan.symbolic()
+        ci, v = plan.numeric(dA.vals, dB.vals)
+        return plan, rp, ci, v
+
+    for _ in range(args.warmup):
+        plan, rp, ci, v = step()
+        plan.close()
+        del rp, ci, v
+    torch.cuda.synchronize()
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    times, ktimes, launches = [], [], 0
+    for _ in range(args.steps):
+        flush.fill_(1)                      # evict L2 between timed steps
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        plan, rp, ci, v = step(profile=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1))
+        ktimes.append(nat.spgemm_plan_kernel_times(plan.handle))
+        launches += nat.spgemm_plan_launches(plan.handle)
+        plan_stats = plan.stats()
+        nnz_c = int(ci.numel())
+        last = (plan, rp, ci, v)
+        plan.close()
+    clocks = sampler.stop()
+    total_ms = float(sum(times))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        pt = torch.tensor([my_products], dtype=torch.float64)
+        dist.all_reduce(pt, op=dist.ReduceOp.SUM)
+        all_products = int(pt.item())
+    else:
+        all_products = my_products
+    ms_per_step = total_ms / args.steps
+    gflops = 2.0 * all_products / (ms_per_step / 1e3) / 1e9
+
+    # dominant kernel and its roofline
+    names = list(ktimes[0].keys())
+    avg = {n: float(np.mean([k[n] for k in ktimes])) for n in names}
+    dom = max((n for n in names if n.startswith("num_") or n.startswith("sym_")), key=lambda n: avg[n])
+    _, rp_last, _, _ = last
+    c_rp = rp_last.cpu().numpy().astype(np.int64)
+    byte_model = kernel_bytes(A, B, prod[rb:re], c_rp, dom, rb)
+    peak, peak_kind = measured_hbm_peak()
+    achieved = byte_model / (avg[dom] / 1e3) / 1e9 if avg[dom] > 0 else 0.0
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind + " hbm_gbs (copy)",
+            "algorithmic_bytes": int(byte_model), "kernel_ms": round(avg[dom], 4),
+            "traffic": traffic_from_profiles(dom, desc["workload"])}
+
+    e2e = run_e2e(args, api, torch, dev, A, B, kw, all_products if world == 1 else my_products)
+    out = {
+        "metric": "SpGEMM GFLOP/s (2*products/s)", "value": round(gflops, 2), "unit": "GFLOP/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded generator, no dataset)",
+        "config": dict(desc, products=int(prod.sum()), nnz_C=nnz_c, l2="flushed between timed steps",
+                       parallelism="row blocks balanced by products" if world > 1 else "single GPU"),
+        "kernel_ms": {n: round(avg[n], 4) for n in names},
+        "rows_per_path": dict(zip(["tiny", "hash", "warp", "block"], plan_stats[2])),
+        "roofline": roof, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks,
+    }
+    return out
+
+
+def kernel_bytes(A, B, prod_rows, c_rp, kernel, row_begin):
+    """Algorithmic bytes of one launch of `kernel` on its rows: the A rows it
+    reads, each B row it touches counted once, and what it writes (numeric:
+    C's columns and values, 12 B per entry for FP64; symbolic: 4 B per row
+    size) -- the byte model of the measurement section, restricted to the
+    kernel's rows."""
+    P = np.asarray(prod_rows, np.int64)
+    path = kernel.split("_", 1)[1]
+    lo, hi = {"tiny": (1, 32), "warp": (33, 8192), "block": (8193, 1 << 62), "hash": (0, -1)}[path]
+    rows = np.flatnonzero((P >= lo) & (P <= hi))
+    if len(rows) == 0:
+        return 0.0
+    arp = A.row_ptr.astype(np.int64)
+    g = rows + row_begin
+    a_nnz = int((arp[g + 1] - arp[g]).sum())
+    idx = np.concatenate([np.arange(arp[r], arp[r + 1]) for r in g]) if len(g) < 20000 else \
+        np.flatnonzero(np.repeat(np.isin(np.arange(A.nrows), g), np.diff(arp)))
+    ks = np.unique(A.col_idx[idx])
+    blens = np.diff(B.row_ptr.astype(np.int64))[ks]
+    numeric = kernel.startswith("num")
+    per_b = 12 if numeric else 4
+    b_bytes = 8 * len(ks) + per_b * int(blens.sum())
+    a_bytes = 8 * len(rows) + (12 if numeric else 4) * a_nnz
+    c_nnz = int((c_rp[rows + 1] - c_rp[rows]).sum())
+    c_bytes = (8 * len(rows) + 12 * c_nnz) if numeric else 4 * len(rows)
+    return float(a_bytes + b_bytes + c_bytes)
+
+
+def traffic_from_profiles(kernel, workload):
+    """dram read+write bytes per launch from a committed ncu summary, if one
+    exists for this kernel and workload and the sources have not changed
+    since; else None."""
+    path = os.path.join(HERE, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+        from paper_2112_10037_gb300 import build as bld
+        ent = rec.get("%s|%s" % (kernel, workload))
+        if ent and ent.get("source_digest") == bld._deps_digest()[:16]:
+            return ent.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def run_e2e(args, api, torch, dev, A, B, kw, products):
+    """Same product through the public API with host buffers: pinned host
+    inputs copied to the device and C copied back inside the timed region."""
+    from paper_2112_10037_gb300 import api as _api  # noqa: F401
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_rp, h_ci, h_v = pin(A.row_ptr), pin(A.col_idx), pin(A.vals)
+    stream = torch.cuda.current_stream()
+    steps = max(1, min(args.steps, 3))
+
+    def once(out=None):
+        d_rp = h_rp.to(dev, non_blocking=True)
+        d_ci = h_ci.to(dev, non_blocking=True)
+        d_v = h_v.to(dev, non_blocking=True)
+        dA = api.DeviceCSR(A.nrows, A.ncols, d_rp, d_ci, d_v)
+        dB = dA if B is A else api.DeviceCSR.from_host(B, device=dev)
+        plan = api.Plan(dA, dB, dtype=torch.float64, **kw)
+        rp, nnz = plan.symbolic()
+        ci, v = plan.numeric(dA.vals, dB.vals)
+        plan.close()
+        if out is None:
+            out = (torch.empty(rp.numel(), dtype=torch.int32).pin_memory(),
+                   torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory(),
+                   torch.empty(max(nnz, 1), dtype=torch.float64).pin_memory())
+        out[0].copy_(rp, non_blocking=True)
+        out[1][:nnz].copy_(ci, non_blocking=True)
+        out[2][:nnz].copy_(v, non_blocking=True)
+        return out, nnz, rp.numel()
+
+    out, nnz, nrp = once()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        once(out)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(ev0.elapsed_time(ev1))
+    ms = float(np.mean(ts))
+    h2d = A.row_ptr.nbytes + A.col_idx.nbytes + A.vals.nbytes
+    d2h = 4 * nrp + 12 * nnz
+    return {"value": round(2.0 * products / (ms / 1e3) / 1e9, 2), "unit": "GFLOP/s",
+            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+# ------------------------------------------------------- reference arm
+def run_reference(args, A, B, desc):
+    """The oracle as it stands (single-threaded C, host cores): each step is
+    the product of a bounded row sample of A with B."""
+    import oracle
+    oracle.build()
+    prod = row_products(A, B)
+    total = int(prod.sum())
+    stride = max(1, int(round(total / 3e8)))   # ~a few seconds per step
+    rows = np.arange(0, A.nrows, stride)
+    sub = oracle.select_rows(A, rows)
+    p = int(prod[rows].sum())
+    for _ in range(args.warmup):
+        oracle.spgemm(sub, B)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.spgemm(sub, B)
+        ts.append(time.perf_counter() - t0)
+    ms = 1e3 * float(np.mean(ts))
+    val = 2.0 * p / (ms / 1e3) / 1e9
+    sample = "rows i = 0 mod %d of A (%d rows, %d products per step)" % (stride, len(rows), p)
+    return {
+        "impl": "reference", "metric": "SpGEMM GFLOP/s (2*products/s)", "value": round(val, 4),
+        "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic (seeded generator, no dataset)", "config": desc,
+        "cpu_baseline": {"value": round(val, 4), "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(val, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "lap2d", "stencil3d"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        A, B, desc = make_workload(args.workload)
+        print(json.dumps(run_reference(args, A, B, desc)), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    A, B, desc = make_workload(args.workload)
+    out = run_ours(args, rank, world, A, B, desc)
+    if rank == 0:
+        if not args.no_cpu and world == 1:
+            out["cpu_baseline"] = cpu_oracle_leg(A, B, row_products(A, B))
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,172 @@
+/*
+ * spgemm.h -- C ABI of the GB300 (sm_103a) Gustavson SpGEMM library.
+ *
+ * C = A * B for sparse matrices in CSR form (Sec. 2.1: values, column
+ * indices, row pointers), computed row by row with the row-wise Gustavson
+ * method (Sec. 2.2): row i of C is the sum, over the nonzeros A(i,k), of the
+ * scaled rows A(i,k) * B(k,:).  Adding sparse rows merges them by column and
+ * adds the values of equal columns (Sec. 2.2, Algorithm 1), so every output
+ * row holds each reached column once, in ascending order.  Entries whose
+ * products cancel to 0.0 are kept: the pattern of C is structural.
+ *
+ * Conventions for every call below
+ *   - Indices are int32.  Row pointers of inputs and of C are int32, so
+ *     nnz(A), nnz(B), nnz(C) must each stay below 2^31; the number of
+ *     products may exceed that (it is counted in int64).
+ *   - Column indices of A and B must be ascending and unique within each
+ *     row, and inside [0, ncols).  With opts.validate set the library checks
+ *     this on the device and reports SPGEMM_ERR_UNSORTED_INPUT.
+ *   - Every pointer to matrix data or workspace is a DEVICE pointer on the
+ *     current CUDA device; c_nnz of spgemm_symbolic is a host pointer.
+ *   - All matrix buffers and the workspace belong to the caller; the library
+ *     never allocates device memory, never frees caller memory and never
+ *     calls cudaDeviceSynchronize.  The plan is library-owned host memory.
+ *   - Work is issued asynchronously on the given stream (a cudaStream_t;
+ *     NULL is the legacy default stream).  Only spgemm_symbolic and
+ *     spgemm_plan_check block, on that stream only.
+ *   - Errors are returned as spgemm_status; nothing aborts and no C++
+ *     exception crosses this boundary.  Faults detected on the device (bad
+ *     input with validate, index overflow, an exhausted probe bound) are
+ *     recorded in a device error word and reported by the next blocking call.
+ */
+#ifndef SPGEMM_GB300_H
+#define SPGEMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* spgemm_stream_t;
+
+typedef enum spgemm_status {
+  SPGEMM_OK = 0,
+  SPGEMM_ERR_INVALID_ARG = 1,     /* NULL pointer, negative size, bad option */
+  SPGEMM_ERR_DIM_MISMATCH = 2,    /* A.ncols != B.nrows, or row range outside A */
+  SPGEMM_ERR_UNSORTED_INPUT = 3,  /* a column index out of range, repeated or descending */
+  SPGEMM_ERR_INDEX_OVERFLOW = 4,  /* nnz(C) (or an input nnz) does not fit int32 */
+  SPGEMM_ERR_WORKSPACE = 5,       /* workspace NULL or smaller than spgemm_workspace_size */
+  SPGEMM_ERR_TABLE_OVERFLOW = 6,  /* a bounded probe or loop gave up (internal limit) */
+  SPGEMM_ERR_CUDA = 7,            /* a CUDA runtime call failed */
+  SPGEMM_ERR_INTERNAL = 8,
+  SPGEMM_ERR_NOT_READY = 9        /* calls out of order (numeric before symbolic) */
+} spgemm_status;
+
+typedef enum spgemm_dtype { SPGEMM_F64 = 0, SPGEMM_F32 = 1 } spgemm_dtype;
+
+/* A CSR matrix (Sec. 2.1).  row_ptr has nrows+1 entries with row_ptr[0] = 0
+ * and row_ptr[nrows] = nnz; col_idx and vals have nnz entries.  vals may be
+ * NULL where a call reads only the structure. */
+typedef struct spgemm_csr {
+  int64_t nrows;
+  int64_t ncols;
+  int64_t nnz;
+  const int32_t* row_ptr;
+  const int32_t* col_idx;
+  const void* vals;
+} spgemm_csr;
+
+/* Tuning and behaviour.  Fill with spgemm_opts_default, then override. */
+typedef struct spgemm_opts {
+  int32_t dtype;       /* spgemm_dtype of A, B and C values */
+  int32_t validate;    /* nonzero: check the column-index preconditions on the device */
+  int64_t row_begin;   /* multiply rows [row_begin, row_end) of A only; C then has */
+  int64_t row_end;     /*   row_end - row_begin rows.  row_end < 0 means A.nrows */
+  int32_t warp_max;    /* rows with at most this many products use one warp per row;
+                          more use a whole block (0: library default) */
+  int32_t force_path;  /* -1: automatic.  Testing overrides: 1 (2) sends every row
+                          above the register-sort limit to the warp (block) path;
+                          3 (4) sends every non-empty row to the warp (block) path */
+  int32_t hash_max;    /* rows of at most this many products use the shared-memory
+                          hash accumulator (0: library default; -1: never) */
+  int32_t window_warp; /* accumulator width (columns) of the warp path, power of two
+                          in [256, 8192] (0: default) */
+  int32_t window_block;/* accumulator width of the block path, power of two in
+                          [1024, 16384] (0: default) */
+  int32_t reserved[7];
+} spgemm_opts;
+
+typedef struct spgemm_plan spgemm_plan;
+
+/* Fills *o with defaults: F64, no validation, all rows, automatic paths. */
+void spgemm_opts_default(spgemm_opts* o);
+
+/* Text for a status code (static storage). */
+const char* spgemm_status_string(spgemm_status s);
+
+/* Library version string, e.g. "0.1.0". */
+const char* spgemm_version(void);
+
+/* Bytes of device workspace a plan for this A, B and options needs.  Host
+ * only, no device work.  The size depends on A.nrows (or the row range) and
+ * A.nnz, not on the values. */
+spgemm_status spgemm_workspace_size(const spgemm_csr* A, const spgemm_csr* B,
+                                    const spgemm_opts* opts, size_t* bytes);
+
+/* Structure analysis of C = A*B (Sec. 2.2; the per-row product count is the
+ * row sum of the per-nonzero B_NUM_VEC of Table 1).  Checks shapes on the
+ * host, then issues on `stream`: per-row product counts and column spans,
+ * the binning of rows by product count, and (with validate) the index
+ * checks.  Creates *plan, which keeps the pointers of A's and B's structure
+ * and of the workspace: they must stay valid and unchanged until
+ * spgemm_plan_destroy.  Does not block. */
+spgemm_status spgemm_analyse(const spgemm_csr* A, const spgemm_csr* B,
+                             const spgemm_opts* opts, void* workspace,
+                             size_t workspace_bytes, spgemm_stream_t stream,
+                             spgemm_plan** plan);
+
+/* Symbolic pass: sizes every row of C (the number of distinct columns the
+ * row's products reach, Sec. 2.2) and writes C's row pointer to c_row_ptr
+ * (device, int32, nrows(C)+1 entries) by an exclusive prefix sum.  BLOCKS on
+ * `stream` to return nnz(C) in *c_nnz (host) and to report any device error
+ * recorded so far.  SPGEMM_ERR_INDEX_OVERFLOW if nnz(C) >= 2^31. */
+spgemm_status spgemm_symbolic(spgemm_plan* plan, int32_t* c_row_ptr, int64_t* c_nnz,
+                              spgemm_stream_t stream);
+
+/* Numeric pass: C's column indices (ascending in each row) and values, for
+ * the values a_vals / b_vals (device, plan dtype, aligned with A's and B's
+ * col_idx).  c_row_ptr is the array spgemm_symbolic wrote; c_col_idx and
+ * c_vals have nnz(C) entries.  Repeatable with new values of the same
+ * structure.  Does not block and allocates nothing, so it may be captured
+ * in a CUDA graph. */
+spgemm_status spgemm_numeric(spgemm_plan* plan, const void* a_vals, const void* b_vals,
+                             const int32_t* c_row_ptr, int32_t* c_col_idx, void* c_vals,
+                             spgemm_stream_t stream);
+
+/* Work statistics of an analysed plan (blocks on `stream` to read them):
+ * total and largest per-row product count, and the number of rows sent to
+ * the register-sort, hash, warp and block paths.  Any output may be NULL. */
+spgemm_status spgemm_plan_stats(spgemm_plan* plan, spgemm_stream_t stream,
+                                int64_t* total_products, int64_t* max_row_products,
+                                int64_t* rows_per_path /* 4 entries */);
+
+/* Per-kernel timing for measurement.  With on != 0 the plan records a pair of
+ * CUDA events (on the launching stream) around each group of kernels it
+ * issues; spgemm_plan_kernel_times then blocks on the last recorded event
+ * and returns the elapsed milliseconds of the most recent call of each group
+ * in ms[0..n-1], in this order: analyse, symbolic register-sort, symbolic
+ * hash, symbolic warp, symbolic block, scan, numeric register-sort, numeric
+ * hash, numeric warp, numeric block (SPGEMM_TIMER_COUNT entries; groups
+ * never run read as 0).  Creating the events is the only resource this
+ * allocates (host-side event handles). */
+#define SPGEMM_TIMER_COUNT 10
+spgemm_status spgemm_plan_set_profiling(spgemm_plan* plan, int on);
+spgemm_status spgemm_plan_kernel_times(spgemm_plan* plan, float* ms, int n);
+
+/* Number of kernel launches this plan has issued since it was created. */
+spgemm_status spgemm_plan_launches(spgemm_plan* plan, int64_t* launches);
+
+/* Blocks on `stream` and returns the device error word as a status. */
+spgemm_status spgemm_plan_check(spgemm_plan* plan, spgemm_stream_t stream);
+
+/* Frees the plan (host memory only).  NULL is allowed. */
+void spgemm_plan_destroy(spgemm_plan* plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPGEMM_GB300_H */

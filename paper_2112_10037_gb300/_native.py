@@ -1,0 +1,174 @@
+"""ctypes binding of the C ABI in ``include/spgemm.h`` -- argument
+marshalling only.  Every function here has the name of the C entry point it
+calls; all computation runs in the CUDA library.
+
+The library is loaded on first use.  If it has not been built, the call
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libspgemm_gb300.so")
+
+SPGEMM_F64 = 0
+SPGEMM_F32 = 1
+
+STATUS_NAMES = {
+    0: "SPGEMM_OK", 1: "SPGEMM_ERR_INVALID_ARG", 2: "SPGEMM_ERR_DIM_MISMATCH",
+    3: "SPGEMM_ERR_UNSORTED_INPUT", 4: "SPGEMM_ERR_INDEX_OVERFLOW", 5: "SPGEMM_ERR_WORKSPACE",
+    6: "SPGEMM_ERR_TABLE_OVERFLOW", 7: "SPGEMM_ERR_CUDA", 8: "SPGEMM_ERR_INTERNAL",
+    9: "SPGEMM_ERR_NOT_READY",
+}
+
+
+class SpgemmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (where, STATUS_NAMES.get(status, status),
+                                          spgemm_status_string(status)))
+
+
+class spgemm_csr(ctypes.Structure):
+    _fields_ = [("nrows", ctypes.c_int64), ("ncols", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("row_ptr", ctypes.c_void_p), ("col_idx", ctypes.c_void_p), ("vals", ctypes.c_void_p)]
+
+
+class spgemm_opts(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("validate", ctypes.c_int32),
+                ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64),
+                ("warp_max", ctypes.c_int32), ("force_path", ctypes.c_int32),
+                ("hash_max", ctypes.c_int32), ("window_warp", ctypes.c_int32),
+                ("window_block", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+_P = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+_SIG = {
+    "spgemm_opts_default": ([ctypes.POINTER(spgemm_opts)], None),
+    "spgemm_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "spgemm_version": ([], ctypes.c_char_p),
+    "spgemm_workspace_size": ([ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
+                               ctypes.POINTER(spgemm_opts), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "spgemm_analyse": ([ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_opts),
+                        _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "spgemm_symbolic": ([_P, _P, _I64P, _P], ctypes.c_int),
+    "spgemm_numeric": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "spgemm_plan_stats": ([_P, _P, _I64P, _I64P, _I64P], ctypes.c_int),
+    "spgemm_plan_check": ([_P, _P], ctypes.c_int),
+    "spgemm_plan_set_profiling": ([_P, ctypes.c_int], ctypes.c_int),
+    "spgemm_plan_kernel_times": ([_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int], ctypes.c_int),
+    "spgemm_plan_launches": ([_P, _I64P], ctypes.c_int),
+    "spgemm_plan_destroy": ([_P], None),
+}
+
+
+def lib():
+    """The loaded CUDA library; raises if it was not built."""
+    global _lib
+    if _lib is None:
+        with _lock:
+            if _lib is None:
+                if not os.path.exists(LIB_PATH):
+                    raise RuntimeError(
+                        "CUDA library %s is missing: build it with "
+                        "`python -m paper_2112_10037_gb300.build`" % LIB_PATH)
+                handle = ctypes.CDLL(LIB_PATH)
+                for name, (args, res) in _SIG.items():
+                    fn = getattr(handle, name)
+                    fn.argtypes = args
+                    fn.restype = res
+                _lib = handle
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise SpgemmError(status, where)
+
+
+# ---------------------------------------------------------------- bindings
+def spgemm_opts_default() -> spgemm_opts:
+    o = spgemm_opts()
+    lib().spgemm_opts_default(ctypes.byref(o))
+    return o
+
+
+def spgemm_status_string(status: int) -> str:
+    return lib().spgemm_status_string(int(status)).decode()
+
+
+def spgemm_version() -> str:
+    return lib().spgemm_version().decode()
+
+
+def spgemm_workspace_size(A: spgemm_csr, B: spgemm_csr, opts: spgemm_opts) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().spgemm_workspace_size(ctypes.byref(A), ctypes.byref(B), ctypes.byref(opts), ctypes.byref(n)),
+           "spgemm_workspace_size")
+    return n.value
+
+
+def spgemm_analyse(A: spgemm_csr, B: spgemm_csr, opts: spgemm_opts, workspace: int, workspace_bytes: int,
+                   stream: int) -> int:
+    plan = _P(None)
+    _check(lib().spgemm_analyse(ctypes.byref(A), ctypes.byref(B), ctypes.byref(opts), _P(workspace),
+                                ctypes.c_size_t(workspace_bytes), _P(stream), ctypes.byref(plan)),
+           "spgemm_analyse")
+    return plan.value
+
+
+def spgemm_symbolic(plan: int, c_row_ptr: int, stream: int) -> int:
+    nnz = ctypes.c_int64(-1)
+    _check(lib().spgemm_symbolic(_P(plan), _P(c_row_ptr), ctypes.byref(nnz), _P(stream)), "spgemm_symbolic")
+    return nnz.value
+
+
+def spgemm_numeric(plan: int, a_vals: int, b_vals: int, c_row_ptr: int, c_col_idx: int, c_vals: int,
+                   stream: int) -> None:
+    _check(lib().spgemm_numeric(_P(plan), _P(a_vals), _P(b_vals), _P(c_row_ptr), _P(c_col_idx), _P(c_vals),
+                                _P(stream)), "spgemm_numeric")
+
+
+def spgemm_plan_stats(plan: int, stream: int):
+    tot, mx = ctypes.c_int64(0), ctypes.c_int64(0)
+    rows = (ctypes.c_int64 * 4)()
+    _check(lib().spgemm_plan_stats(_P(plan), _P(stream), ctypes.byref(tot), ctypes.byref(mx), rows),
+           "spgemm_plan_stats")
+    return tot.value, mx.value, list(rows)
+
+
+def spgemm_plan_check(plan: int, stream: int) -> None:
+    _check(lib().spgemm_plan_check(_P(plan), _P(stream)), "spgemm_plan_check")
+
+
+SPGEMM_TIMER_COUNT = 10
+TIMER_NAMES = ["analyse", "sym_tiny", "sym_hash", "sym_warp", "sym_block", "scan",
+               "num_tiny", "num_hash", "num_warp", "num_block"]
+
+
+def spgemm_plan_set_profiling(plan: int, on: bool) -> None:
+    _check(lib().spgemm_plan_set_profiling(_P(plan), 1 if on else 0), "spgemm_plan_set_profiling")
+
+
+def spgemm_plan_kernel_times(plan: int):
+    ms = (ctypes.c_float * SPGEMM_TIMER_COUNT)()
+    _check(lib().spgemm_plan_kernel_times(_P(plan), ms, SPGEMM_TIMER_COUNT), "spgemm_plan_kernel_times")
+    return dict(zip(TIMER_NAMES, list(ms)))
+
+
+def spgemm_plan_launches(plan: int) -> int:
+    n = ctypes.c_int64(0)
+    _check(lib().spgemm_plan_launches(_P(plan), ctypes.byref(n)), "spgemm_plan_launches")
+    return n.value
+
+
+def spgemm_plan_destroy(plan: int) -> None:
+    if plan:
+        lib().spgemm_plan_destroy(_P(plan))

@@ -1,0 +1,156 @@
+// Structure analysis: input validation, per-row product counts and column
+// spans, and the counting sort of rows into bins by product count.
+//
+// The product count of row i is P_i = sum over the nonzeros A(i,k) of
+// nnz(B(k,:)) -- the number of scalar-times-row products the row-wise
+// Gustavson method (Sec. 2.2) forms for that row (the per-nonzero
+// B_NUM_VEC of Table 1, summed).  Rows are later dispatched by P_i.
+#include "internal.cuh"
+
+namespace sg {
+
+// One warp per row: column indices inside [0, ncols), strictly ascending;
+// row_ptr non-decreasing and ending at nnz.
+__global__ void k_validate(Csr M, uint32_t* err) {
+  const int lane = lane_id();
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
+  bool bad = false;
+  if (w == 0 && lane == 0) {
+    if (M.rp[0] != 0 || (long long)M.rp[M.nrows] != M.nnz) bad = true;
+  }
+  for (long long i = w; i < M.nrows; i += nw) {
+    const int a0 = M.rp[i], a1 = M.rp[i + 1];
+    if (a1 < a0 || a0 < 0 || (long long)a1 > M.nnz) { bad = true; continue; }
+    for (int e = a0 + lane; e < a1; e += 32) {
+      const int c = M.ci[e];
+      if (c < 0 || (long long)c >= M.ncols) bad = true;
+      if (e > a0 && M.ci[e - 1] >= c) bad = true;
+    }
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, EB_UNSORTED);
+}
+
+// One warp per row of A: P_i, the smallest and largest column any product
+// of the row reaches (first and last column of each touched B row, since B's
+// rows are sorted), histogram of bins, total and maximum P.
+__global__ void __launch_bounds__(256) k_analyse(Csr A, Csr B, long long row_begin, long long mloc,
+                                                 long long* __restrict__ prod, int* __restrict__ cmin,
+                                                 int* __restrict__ cmax, DevStats* st) {
+  __shared__ int s_hist[NBINS];
+  __shared__ unsigned long long s_total, s_max;
+  if (threadIdx.x < NBINS) s_hist[threadIdx.x] = 0;
+  if (threadIdx.x == 0) { s_total = 0; s_max = 0; }
+  if (block_skip(st)) return;  // validated input was rejected
+  const int lane = lane_id();
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
+  unsigned long long my_total = 0, my_max = 0;
+  bool bad = false;
+  for (long long r = w; r < mloc; r += nw) {
+    const long long i = row_begin + r;
+    const int a0 = A.rp[i], a1 = A.rp[i + 1];
+    long long p = 0;
+    int mn = INT_MAX, mx = -1;
+    for (int e = a0 + lane; e < a1; e += 32) {
+      const int k = A.ci[e];
+      if (k < 0 || (long long)k >= B.nrows) { bad = true; continue; }
+      const int s = B.rp[k], t = B.rp[k + 1];
+      if (t > s) {
+        p += t - s;
+        mn = min(mn, B.ci[s]);
+        mx = max(mx, B.ci[t - 1]);
+      }
+    }
+    p = warp_sum(p);
+    mn = warp_min(mn);
+    mx = warp_max(mx);
+    if (lane == 0) {
+      prod[r] = p;
+      cmin[r] = mn;
+      cmax[r] = mx;
+      atomicAdd(&s_hist[bin_of(p)], 1);
+      my_total += (unsigned long long)p;
+      my_max = my_max > (unsigned long long)p ? my_max : (unsigned long long)p;
+    }
+  }
+  if (lane == 0 && my_total) {
+    atomicAdd(&s_total, my_total);
+    atomicMax(&s_max, my_max);
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicOr(&st->err, EB_UNSORTED);
+  __syncthreads();
+  if (threadIdx.x < NBINS && s_hist[threadIdx.x]) atomicAdd(&st->hist[threadIdx.x], s_hist[threadIdx.x]);
+  if (threadIdx.x == 0 && s_total) {
+    atomicAdd(&st->total_products, s_total);
+    atomicMax(&st->max_products, s_max);
+  }
+}
+
+// Counting sort of the non-empty rows by bin, largest bin first.  Each block
+// takes a contiguous chunk of rows: counts per bin in shared memory, reserves
+// one range per bin with a single global atomic, then places its rows.
+constexpr int SCATTER_ROWS = 4096;
+
+__global__ void __launch_bounds__(256) k_bin_scatter(const long long* __restrict__ prod, long long mloc,
+                                                     DevStats* st, int* __restrict__ rows) {
+  __shared__ int s_start[NBINS];
+  __shared__ int s_cnt[NBINS];
+  __shared__ int s_base[NBINS];
+  if (block_skip(st)) return;
+  if (threadIdx.x < NBINS) {
+    int b = threadIdx.x, acc = 0;
+    for (int k = NBINS - 1; k > b; --k) acc += st->hist[k];
+    s_start[b] = acc;
+    s_cnt[b] = 0;
+  }
+  __syncthreads();
+  const long long r0 = (long long)blockIdx.x * SCATTER_ROWS;
+  const long long r1 = min(mloc, r0 + SCATTER_ROWS);
+  for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const int b = bin_of(prod[r]);
+    if (b) atomicAdd(&s_cnt[b], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < NBINS) {
+    const int b = threadIdx.x;
+    s_base[b] = s_cnt[b] ? s_start[b] + atomicAdd(&st->fill[b], s_cnt[b]) : 0;
+    s_cnt[b] = 0;
+  }
+  __syncthreads();
+  for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    const int b = bin_of(prod[r]);
+    if (b) rows[s_base[b] + atomicAdd(&s_cnt[b], 1)] = (int)r;
+  }
+}
+
+static int grid_for_warps(long long nwarps, int warps_per_block, int nsm) {
+  long long blocks = (nwarps + warps_per_block - 1) / warps_per_block;
+  long long cap = (long long)nsm * 8;
+  if (blocks > cap) blocks = cap;
+  return (int)(blocks < 1 ? 1 : blocks);
+}
+
+cudaError_t launch_validate(const LaunchCtx& c, const Csr& M) {
+  k_validate<<<grid_for_warps(M.nrows > 0 ? M.nrows : 1, 8, c.nsm), 256, 0, c.stream>>>(M, c.err);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_analyse(const LaunchCtx& c, const Csr& A, const Csr& B, long long row_begin,
+                           long long mloc, long long* prod, int* cmin, int* cmax, int* rows) {
+  if (mloc <= 0) return cudaSuccess;
+  timer_mark(c, T_ANALYSE, 0);
+  k_analyse<<<grid_for_warps(mloc, 8, c.nsm), 256, 0, c.stream>>>(A, B, row_begin, mloc, prod, cmin,
+                                                                   cmax, c.st);
+  count_launch(c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const long long blocks = (mloc + SCATTER_ROWS - 1) / SCATTER_ROWS;
+  k_bin_scatter<<<(unsigned)blocks, 256, 0, c.stream>>>(prod, mloc, c.st, rows);
+  count_launch(c);
+  timer_mark(c, T_ANALYSE, 1);
+  return cudaGetLastError();
+}
+
+}  // namespace sg

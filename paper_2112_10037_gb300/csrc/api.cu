@@ -1,0 +1,347 @@
+// C ABI of the library (declared in include/spgemm.h): argument checks,
+// workspace carving, plan state and the order of the passes.
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "internal.cuh"
+
+struct spgemm_plan {
+  int device = 0;
+  int nsm = 0;
+  sg::Csr A{}, B{};
+  spgemm_opts opts{};
+  long long row_begin = 0, mloc = 0;
+  // carved workspace
+  unsigned char* ws = nullptr;
+  size_t ws_bytes = 0;
+  sg::DevStats* st = nullptr;
+  long long* prod = nullptr;
+  int* cmin = nullptr;
+  int* cmax = nullptr;
+  int* rows = nullptr;
+  int32_t* cursor = nullptr;
+  long long* scan_part = nullptr;
+  // host state
+  sg::PathBins pb{};
+  sg::Tuning tu{};
+  bool symbolic_done = false;
+  long long nnz_c = -1;
+  int path_rows[sg::NPATHS] = {0, 0, 0, 0};
+  sg::DevStats host_st{};
+  // measurement
+  bool profiling = false;
+  cudaEvent_t timers[2 * sg::NTIMERS] = {};
+  int timer_used[sg::NTIMERS] = {};
+  long long launches = 0;
+
+  ~spgemm_plan() {
+    for (auto& ev : timers)
+      if (ev) cudaEventDestroy(ev);
+  }
+};
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
+
+struct Layout {
+  size_t st, prod, cmin, cmax, rows, cursor, scan, total;
+};
+
+Layout layout_for(long long mloc, long long nnz_a) {
+  Layout L{};
+  size_t off = 0;
+  L.st = off; off = align_up(off + sizeof(sg::DevStats));
+  L.prod = off; off = align_up(off + sizeof(long long) * (size_t)mloc);
+  L.cmin = off; off = align_up(off + sizeof(int) * (size_t)mloc);
+  L.cmax = off; off = align_up(off + sizeof(int) * (size_t)mloc);
+  L.rows = off; off = align_up(off + sizeof(int) * (size_t)mloc);
+  L.cursor = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
+  L.scan = off; off = align_up(off + sizeof(long long) * sg::scan_partials_count(mloc));
+  L.total = off;
+  return L;
+}
+
+int sm_count_for(int dev) {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  if (dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> g(mu);
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) cache[dev] = n;
+  }
+  return cache[dev];
+}
+
+spgemm_status check_csr(const spgemm_csr* M) {
+  if (!M) return SPGEMM_ERR_INVALID_ARG;
+  if (M->nrows < 0 || M->ncols < 0 || M->nnz < 0) return SPGEMM_ERR_INVALID_ARG;
+  if (M->nrows >= (1ll << 31) - 1 || M->ncols >= (1ll << 31) - 1 || M->nnz >= (1ll << 31))
+    return SPGEMM_ERR_INDEX_OVERFLOW;
+  if (!M->row_ptr) return SPGEMM_ERR_INVALID_ARG;
+  if (M->nnz > 0 && !M->col_idx) return SPGEMM_ERR_INVALID_ARG;
+  return SPGEMM_OK;
+}
+
+int pow2_at_least(int v, int lo, int hi) {
+  int p = lo;
+  while (p < v && p < hi) p <<= 1;
+  return p;
+}
+
+// Bin ranges of the paths from the options (see sg::bin_of for the bins).
+void choose_paths(const spgemm_opts& o, sg::PathBins* pb, sg::Tuning* tu) {
+  const int last = sg::NBINS - 1;
+  tu->warp_max = o.warp_max > 0 ? o.warp_max : 8192;
+  tu->window_warp = o.window_warp > 0 ? pow2_at_least(o.window_warp, 512, 2048) : 1024;
+  tu->window_block = o.window_block > 0 ? pow2_at_least(o.window_block, 4096, 16384) : 8192;
+  tu->hash_max = 0;
+  const int wb = sg::bin_of(tu->warp_max) < 7 ? 7 : sg::bin_of(tu->warp_max);
+  for (int p = 0; p < sg::NPATHS; ++p) { pb->lo[p] = 1; pb->hi[p] = 0; }
+  switch (o.force_path) {
+    case 1: pb->lo[sg::PATH_TINY] = 1; pb->hi[sg::PATH_TINY] = 6; pb->lo[sg::PATH_WARP] = 7; pb->hi[sg::PATH_WARP] = last; break;
+    case 2: pb->lo[sg::PATH_TINY] = 1; pb->hi[sg::PATH_TINY] = 6; pb->lo[sg::PATH_BLOCK] = 7; pb->hi[sg::PATH_BLOCK] = last; break;
+    case 3: pb->lo[sg::PATH_WARP] = 1; pb->hi[sg::PATH_WARP] = last; break;
+    case 4: pb->lo[sg::PATH_BLOCK] = 1; pb->hi[sg::PATH_BLOCK] = last; break;
+    default:
+      pb->lo[sg::PATH_TINY] = 1; pb->hi[sg::PATH_TINY] = 6;
+      pb->lo[sg::PATH_WARP] = 7; pb->hi[sg::PATH_WARP] = wb;
+      pb->lo[sg::PATH_BLOCK] = wb + 1; pb->hi[sg::PATH_BLOCK] = last;
+      break;
+  }
+}
+
+spgemm_status from_err_word(uint32_t w) {
+  if (w & sg::EB_UNSORTED) return SPGEMM_ERR_UNSORTED_INPUT;
+  if (w & sg::EB_OVERFLOW) return SPGEMM_ERR_INDEX_OVERFLOW;
+  if (w & sg::EB_TABLE) return SPGEMM_ERR_TABLE_OVERFLOW;
+  if (w & sg::EB_INTERNAL) return SPGEMM_ERR_INTERNAL;
+  return SPGEMM_OK;
+}
+
+sg::LaunchCtx ctx_of(spgemm_plan* p, spgemm_stream_t s) {
+  sg::LaunchCtx c;
+  c.stream = (cudaStream_t)s;
+  c.nsm = p->nsm;
+  c.st = p->st;
+  c.err = &p->st->err;
+  c.timers = p->profiling ? p->timers : nullptr;
+  c.timer_used = p->timer_used;
+  c.launches = &p->launches;
+  return c;
+}
+
+sg::RowInfo rowinfo_of(const spgemm_plan* p) {
+  sg::RowInfo ri;
+  ri.row_begin = p->row_begin;
+  ri.mloc = p->mloc;
+  ri.prod = p->prod;
+  ri.cmin = p->cmin;
+  ri.cmax = p->cmax;
+  ri.rows = p->rows;
+  return ri;
+}
+
+spgemm_status read_stats(spgemm_plan* p, cudaStream_t s) {
+  if (cudaMemcpyAsync(&p->host_st, p->st, sizeof(sg::DevStats), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return SPGEMM_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  for (int q = 0; q < sg::NPATHS; ++q) {
+    int n = 0;
+    for (int b = p->pb.lo[q]; b <= p->pb.hi[q]; ++b) n += p->host_st.hist[b];
+    p->path_rows[q] = n;
+  }
+  return SPGEMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void spgemm_opts_default(spgemm_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->dtype = SPGEMM_F64;
+  o->validate = 0;
+  o->row_begin = 0;
+  o->row_end = -1;
+  o->warp_max = 0;
+  o->force_path = -1;
+  o->hash_max = 0;
+  o->window_warp = 0;
+  o->window_block = 0;
+}
+
+const char* spgemm_status_string(spgemm_status s) {
+  switch (s) {
+    case SPGEMM_OK: return "ok";
+    case SPGEMM_ERR_INVALID_ARG: return "invalid argument";
+    case SPGEMM_ERR_DIM_MISMATCH: return "dimension mismatch";
+    case SPGEMM_ERR_UNSORTED_INPUT: return "column indices out of range, repeated or not ascending";
+    case SPGEMM_ERR_INDEX_OVERFLOW: return "index overflow (a count does not fit int32)";
+    case SPGEMM_ERR_WORKSPACE: return "workspace missing or too small";
+    case SPGEMM_ERR_TABLE_OVERFLOW: return "bounded probe limit reached";
+    case SPGEMM_ERR_CUDA: return "CUDA runtime error";
+    case SPGEMM_ERR_INTERNAL: return "internal error";
+    case SPGEMM_ERR_NOT_READY: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* spgemm_version(void) { return "0.1.0"; }
+
+spgemm_status spgemm_workspace_size(const spgemm_csr* A, const spgemm_csr* B, const spgemm_opts* opts,
+                                    size_t* bytes) {
+  if (!bytes) return SPGEMM_ERR_INVALID_ARG;
+  spgemm_status s;
+  if ((s = check_csr(A)) != SPGEMM_OK) return s;
+  if ((s = check_csr(B)) != SPGEMM_OK) return s;
+  spgemm_opts o;
+  if (opts) o = *opts; else spgemm_opts_default(&o);
+  const long long rb = o.row_begin, re = o.row_end < 0 ? A->nrows : o.row_end;
+  if (rb < 0 || re < rb || re > A->nrows) return SPGEMM_ERR_DIM_MISMATCH;
+  *bytes = layout_for(re - rb, A->nnz).total;
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_analyse(const spgemm_csr* A, const spgemm_csr* B, const spgemm_opts* opts,
+                             void* workspace, size_t workspace_bytes, spgemm_stream_t stream,
+                             spgemm_plan** plan) {
+  if (!plan) return SPGEMM_ERR_INVALID_ARG;
+  *plan = nullptr;
+  spgemm_status s;
+  if ((s = check_csr(A)) != SPGEMM_OK) return s;
+  if ((s = check_csr(B)) != SPGEMM_OK) return s;
+  if (A->ncols != B->nrows) return SPGEMM_ERR_DIM_MISMATCH;
+  spgemm_opts o;
+  if (opts) o = *opts; else spgemm_opts_default(&o);
+  if (o.dtype != SPGEMM_F64 && o.dtype != SPGEMM_F32) return SPGEMM_ERR_INVALID_ARG;
+  if (o.force_path < -1 || o.force_path > 4) return SPGEMM_ERR_INVALID_ARG;
+  const long long rb = o.row_begin, re = o.row_end < 0 ? A->nrows : o.row_end;
+  if (rb < 0 || re < rb || re > A->nrows) return SPGEMM_ERR_DIM_MISMATCH;
+  const Layout L = layout_for(re - rb, A->nnz);
+  if (!workspace || workspace_bytes < L.total) return SPGEMM_ERR_WORKSPACE;
+  if (((uintptr_t)workspace) % 16) return SPGEMM_ERR_WORKSPACE;
+
+  spgemm_plan* p = new (std::nothrow) spgemm_plan();
+  if (!p) return SPGEMM_ERR_INTERNAL;
+  if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return SPGEMM_ERR_CUDA; }
+  p->nsm = sm_count_for(p->device);
+  if (p->nsm <= 0) { delete p; return SPGEMM_ERR_CUDA; }
+  p->A = sg::Csr{A->row_ptr, A->col_idx, A->nrows, A->ncols, A->nnz};
+  p->B = sg::Csr{B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz};
+  p->opts = o;
+  p->row_begin = rb;
+  p->mloc = re - rb;
+  p->ws = (unsigned char*)workspace;
+  p->ws_bytes = workspace_bytes;
+  p->st = (sg::DevStats*)(p->ws + L.st);
+  p->prod = (long long*)(p->ws + L.prod);
+  p->cmin = (int*)(p->ws + L.cmin);
+  p->cmax = (int*)(p->ws + L.cmax);
+  p->rows = (int*)(p->ws + L.rows);
+  p->cursor = (int32_t*)(p->ws + L.cursor);
+  p->scan_part = (long long*)(p->ws + L.scan);
+  choose_paths(o, &p->pb, &p->tu);
+
+  cudaStream_t st = (cudaStream_t)stream;
+  sg::LaunchCtx c = ctx_of(p, stream);
+  cudaError_t e = cudaMemsetAsync(p->st, 0, sizeof(sg::DevStats), st);
+  if (e == cudaSuccess && o.validate) {
+    e = sg::launch_validate(c, p->A);
+    if (e == cudaSuccess) e = sg::launch_validate(c, p->B);
+  }
+  if (e == cudaSuccess) e = sg::launch_analyse(c, p->A, p->B, p->row_begin, p->mloc, p->prod, p->cmin, p->cmax, p->rows);
+  if (e != cudaSuccess) { delete p; return SPGEMM_ERR_CUDA; }
+  *plan = p;
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_symbolic(spgemm_plan* p, int32_t* c_row_ptr, int64_t* c_nnz, spgemm_stream_t stream) {
+  if (!p || !c_row_ptr || !c_nnz) return SPGEMM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  sg::LaunchCtx c = ctx_of(p, stream);
+  const sg::RowInfo ri = rowinfo_of(p);
+  cudaError_t e = cudaMemsetAsync(c_row_ptr, 0, sizeof(int32_t) * (size_t)(p->mloc + 1), st);
+  if (e == cudaSuccess && p->mloc > 0)
+    e = sg::launch_symbolic(c, p->A, p->B, ri, p->pb, p->tu, p->cursor, c_row_ptr, nullptr);
+  if (e == cudaSuccess) e = sg::launch_scan(c, c_row_ptr, p->mloc, p->scan_part);
+  if (e != cudaSuccess) return SPGEMM_ERR_CUDA;
+  spgemm_status s = read_stats(p, st);
+  if (s != SPGEMM_OK) return s;
+  s = from_err_word(p->host_st.err);
+  if (s != SPGEMM_OK) return s;
+  p->nnz_c = p->host_st.nnz_c;
+  *c_nnz = p->nnz_c;
+  p->symbolic_done = true;
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_numeric(spgemm_plan* p, const void* a_vals, const void* b_vals, const int32_t* c_row_ptr,
+                             int32_t* c_col_idx, void* c_vals, spgemm_stream_t stream) {
+  if (!p) return SPGEMM_ERR_INVALID_ARG;
+  if (!p->symbolic_done) return SPGEMM_ERR_NOT_READY;
+  if (!c_row_ptr) return SPGEMM_ERR_INVALID_ARG;
+  if (p->nnz_c == 0) return SPGEMM_OK;
+  if (!a_vals || !b_vals || !c_col_idx || !c_vals) return SPGEMM_ERR_INVALID_ARG;
+  sg::LaunchCtx c = ctx_of(p, stream);
+  const sg::RowInfo ri = rowinfo_of(p);
+  cudaError_t e = sg::launch_numeric(c, p->A, p->B, ri, p->pb, p->tu, p->opts.dtype, a_vals, b_vals, p->cursor,
+                                     c_row_ptr, c_col_idx, c_vals, p->path_rows);
+  return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
+}
+
+spgemm_status spgemm_plan_stats(spgemm_plan* p, spgemm_stream_t stream, int64_t* total_products,
+                                int64_t* max_row_products, int64_t* rows_per_path) {
+  if (!p) return SPGEMM_ERR_INVALID_ARG;
+  spgemm_status s = read_stats(p, (cudaStream_t)stream);
+  if (s != SPGEMM_OK) return s;
+  if (total_products) *total_products = (int64_t)p->host_st.total_products;
+  if (max_row_products) *max_row_products = (int64_t)p->host_st.max_products;
+  if (rows_per_path)
+    for (int q = 0; q < sg::NPATHS; ++q) rows_per_path[q] = p->path_rows[q];
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_plan_check(spgemm_plan* p, spgemm_stream_t stream) {
+  if (!p) return SPGEMM_ERR_INVALID_ARG;
+  uint32_t w = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&w, &p->st->err, sizeof(w), cudaMemcpyDeviceToHost, st) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  return from_err_word(w);
+}
+
+spgemm_status spgemm_plan_set_profiling(spgemm_plan* p, int on) {
+  if (!p) return SPGEMM_ERR_INVALID_ARG;
+  if (on && !p->timers[0]) {
+    for (auto& ev : p->timers)
+      if (cudaEventCreate(&ev) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  }
+  p->profiling = on != 0;
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_plan_kernel_times(spgemm_plan* p, float* ms, int n) {
+  if (!p || !ms || n < 0) return SPGEMM_ERR_INVALID_ARG;
+  for (int t = 0; t < n; ++t) {
+    ms[t] = 0.0f;
+    if (t >= sg::NTIMERS || !p->timer_used[t] || !p->timers[0]) continue;
+    if (cudaEventSynchronize(p->timers[2 * t + 1]) != cudaSuccess) return SPGEMM_ERR_CUDA;
+    if (cudaEventElapsedTime(&ms[t], p->timers[2 * t], p->timers[2 * t + 1]) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  }
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_plan_launches(spgemm_plan* p, int64_t* launches) {
+  if (!p || !launches) return SPGEMM_ERR_INVALID_ARG;
+  *launches = p->launches;
+  return SPGEMM_OK;
+}
+
+void spgemm_plan_destroy(spgemm_plan* p) { delete p; }
+
+}  // extern "C"

@@ -1,0 +1,204 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the C ABI (include/spgemm.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <climits>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/spgemm.h"
+
+namespace sg {
+
+// Rows are binned by their product count P (Sec. 2.2: the number of
+// scalar-times-row products that build row i; Table 1's B_NUM_VEC summed
+// over the row).  bin 0 holds P = 0; bin b >= 1 holds P in (2^(b-2), 2^(b-1)],
+// i.e. bin 1: P = 1, bin 2: P = 2, bin 3: P in [3,4], ... ; the last bin takes
+// everything larger.
+constexpr int NBINS = 48;
+
+__host__ __device__ inline int bin_of(long long p) {
+  if (p <= 0) return 0;
+  int b;
+#ifdef __CUDA_ARCH__
+  b = (p == 1) ? 1 : (64 - __clzll(p - 1)) + 1;
+#else
+  b = (p == 1) ? 1 : (64 - __builtin_clzll((unsigned long long)(p - 1))) + 1;
+#endif
+  return b < NBINS ? b : NBINS - 1;
+}
+
+// Error bits of the device error word.
+enum : uint32_t {
+  EB_UNSORTED = 1u,   // column index out of range / not ascending / row_ptr broken
+  EB_OVERFLOW = 2u,   // nnz(C) >= 2^31
+  EB_TABLE = 4u,      // a bounded probe or loop gave up
+  EB_INTERNAL = 8u,   // symbolic and numeric disagree, or an output bound was hit
+};
+
+// Small device-resident statistics block at the start of the workspace.
+struct DevStats {
+  unsigned long long total_products;
+  unsigned long long max_products;
+  long long nnz_c;
+  uint32_t err;
+  uint32_t pad;
+  int hist[NBINS];   // rows per bin
+  int fill[NBINS];   // scatter cursors
+  unsigned int work[8];  // dynamic work counters (reset before each use)
+};
+
+// Paths a non-empty row can take.
+enum Path : int { PATH_TINY = 0, PATH_HASH = 1, PATH_WARP = 2, PATH_BLOCK = 3, NPATHS = 4 };
+
+struct Csr {
+  const int32_t* rp;
+  const int32_t* ci;
+  long long nrows;
+  long long ncols;
+  long long nnz;
+};
+
+// Per-row analysis arrays (all of length mloc, indexed by the local row r).
+struct RowInfo {
+  long long row_begin;   // global row of A = row_begin + r
+  long long mloc;
+  const long long* prod; // products per row
+  const int* cmin;       // smallest column any product reaches
+  const int* cmax;       // largest column any product reaches
+  const int* rows;       // local rows ordered by descending bin
+};
+
+// Bin ranges of each path, computed on the host from the options.
+struct PathBins {
+  int lo[NPATHS];
+  int hi[NPATHS];  // inclusive; hi < lo means the path is unused
+};
+
+// Window widths (columns) of the dense-window accumulators.
+struct Tuning {
+  int window_warp;     // numeric, one warp per row
+  int window_block;    // numeric, one block per row
+  int hash_max;        // largest P of the hash path (0: path disabled)
+  int warp_max;        // largest P of the warp path
+};
+
+// ---------------------------------------------------------------- warp utils
+constexpr unsigned FULL = 0xffffffffu;
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_incl_scan(V v) {
+  const int lane = lane_id();
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    V t = __shfl_up_sync(FULL, v, d);
+    if (lane >= d) v += t;
+  }
+  return v;
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
+  return v;
+}
+
+__device__ __forceinline__ int warp_min(int v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = min(v, __shfl_xor_sync(FULL, v, d));
+  return v;
+}
+
+__device__ __forceinline__ int warp_max(int v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v = max(v, __shfl_xor_sync(FULL, v, d));
+  return v;
+}
+
+// Index of the first lane whose inclusive prefix `incl` exceeds p (incl is
+// non-decreasing over the 32 lanes).  Every lane must call it.
+__device__ __forceinline__ int warp_owner(int incl, int p) {
+  int lo = 0;
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    int t = __shfl_sync(FULL, incl, lo + s - 1);
+    if (t <= p) lo += s;
+  }
+  return lo;
+}
+
+// Block-uniform check of the error word (one read by thread 0, shared with
+// the block through a barrier), so a block never splits around a barrier.
+// Kernels call it first and return when the input was rejected.
+__device__ __forceinline__ bool block_skip(const DevStats* st) {
+  __shared__ int s_skip;
+  if (threadIdx.x == 0) s_skip = (*(volatile const uint32_t*)&st->err & EB_UNSORTED) != 0;
+  __syncthreads();
+  return s_skip != 0;
+}
+
+// [begin, end) of the rows of bins [lo, hi] inside the descending-bin list.
+__device__ __forceinline__ void bin_range(const DevStats* st, int lo, int hi, int* begin, int* end) {
+  int b = 0, e = 0;
+  for (int k = NBINS - 1; k >= 1; --k) {
+    int h = st->hist[k];
+    if (k > hi) b += h;
+    else if (k >= lo) e += h;
+  }
+  *begin = b;
+  *end = b + e;
+}
+
+// ------------------------------------------------------------ host launchers
+struct LaunchCtx {
+  cudaStream_t stream;
+  int nsm;
+  DevStats* st;
+  uint32_t* err;
+  cudaEvent_t* timers;   // 2 events per timer group, or null (profiling off)
+  int* timer_used;       // set to 1 for each group recorded by this call
+  long long* launches;   // kernel launch counter (host)
+};
+
+// Timer groups (the order of spgemm_plan_kernel_times).
+enum Timer : int {
+  T_ANALYSE = 0, T_SYM_TINY = 1, T_SYM_HASH = 2, T_SYM_WARP = 3, T_SYM_BLOCK = 4, T_SCAN = 5,
+  T_NUM_TINY = 6, T_NUM_HASH = 7, T_NUM_WARP = 8, T_NUM_BLOCK = 9, NTIMERS = 10
+};
+
+inline void timer_mark(const LaunchCtx& c, int t, int end) {
+  if (c.timers) {
+    cudaEventRecord(c.timers[2 * t + end], c.stream);
+    if (c.timer_used) c.timer_used[t] = 1;
+  }
+}
+
+inline void count_launch(const LaunchCtx& c) {
+  if (c.launches) ++*c.launches;
+}
+
+cudaError_t launch_validate(const LaunchCtx& c, const Csr& M);
+cudaError_t launch_analyse(const LaunchCtx& c, const Csr& A, const Csr& B, long long row_begin,
+                           long long mloc, long long* prod, int* cmin, int* cmax, int* rows);
+cudaError_t launch_symbolic(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
+                            const PathBins& pb, const Tuning& tu, int32_t* cursor,
+                            int32_t* c_rp, const int* path_rows /* host, may be null */);
+cudaError_t launch_scan(const LaunchCtx& c, int32_t* c_rp, long long mloc, long long* partials);
+size_t scan_partials_count(long long mloc);
+cudaError_t launch_numeric(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
+                           const PathBins& pb, const Tuning& tu, int dtype, const void* av,
+                           const void* bv, int32_t* cursor, const int32_t* c_rp, int32_t* c_ci,
+                           void* c_v, const int* path_rows /* host, may be null */);
+
+
+}  // namespace sg

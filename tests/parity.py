@@ -1,0 +1,50 @@
+"""Comparison helpers for GPU-vs-oracle parity (imported by the tests)."""
+import numpy as np
+
+from paper_2112_10037_gb300 import gen
+
+# FP64 criterion: |c - c*| <= RTOL_F64 * max(|c*|, sum_k |A(i,k) B(k,j)|).
+# With all terms of one sign this is the plain 1e-12 relative bound; the
+# sum-of-magnitudes form keeps near-cancelling sums of N(0,1) products from
+# failing on a tiny |c*|.
+RTOL_F64 = 1e-12
+# FP32 values (accumulated in FP32) against the FP64 oracle: a row of m
+# products carries at most about m * 2^-24 relative error of the magnitude
+# sum; the tests use the bound below for rows of up to a few thousand terms.
+RTOL_F32 = 2e-4
+
+
+def abs_csr(m):
+    return gen.CSR(m.nrows, m.ncols, m.row_ptr, m.col_idx, np.abs(np.asarray(m.vals, np.float64)))
+
+
+def oracle_with_scale(oracle, A, B):
+    """Oracle product and the per-entry magnitude sum (the oracle applied to
+    |A| and |B|, which has the same pattern)."""
+    C = oracle.spgemm(A, B)
+    S = oracle.spgemm(abs_csr(A), abs_csr(B))
+    return C, S.vals
+
+
+def assert_structure_equal(got, ref):
+    assert got.nrows == ref.nrows and got.ncols == ref.ncols
+    assert np.array_equal(np.asarray(got.row_ptr, np.int64), np.asarray(ref.row_ptr, np.int64)), "row_ptr differs"
+    assert np.array_equal(np.asarray(got.col_idx, np.int64), np.asarray(ref.col_idx, np.int64)), "col_idx differs"
+
+
+def max_rel_err(got_vals, ref_vals, scale):
+    got = np.asarray(got_vals, np.float64)
+    ref = np.asarray(ref_vals, np.float64)
+    den = np.maximum(np.abs(ref), np.asarray(scale, np.float64))
+    den = np.where(den == 0, 1.0, den)
+    return float(np.max(np.abs(got - ref) / den)) if len(ref) else 0.0
+
+
+def assert_values_close(got_vals, ref_vals, scale, rtol=RTOL_F64):
+    err = max_rel_err(got_vals, ref_vals, scale)
+    assert err <= rtol, "max relative error %.3e > %.1e" % (err, rtol)
+    return err
+
+
+def assert_values_exact(got_vals, ref_vals):
+    assert np.array_equal(np.asarray(got_vals, np.float64), np.asarray(ref_vals, np.float64))

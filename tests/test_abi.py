@@ -1,0 +1,72 @@
+"""The C-ABI library loads without a GPU and exports every function that
+include/spgemm.h declares; host-side argument checks need no device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2112_10037_gb300 import build as bld
+from paper_2112_10037_gb300 import _native as nat
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "spgemm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(spgemm_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return bld.build()
+
+
+def test_header_declares_entry_points():
+    names = declared_functions()
+    for must in ("spgemm_analyse", "spgemm_symbolic", "spgemm_numeric", "spgemm_workspace_size",
+                 "spgemm_plan_destroy", "spgemm_status_string"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header(libpath):
+    # every declared entry point has a same-named Python binding
+    names = declared_functions()
+    assert not [n for n in names if not hasattr(nat, n)]
+
+
+def test_host_checks_without_gpu(libpath):
+    o = nat.spgemm_opts_default()
+    assert o.dtype == nat.SPGEMM_F64 and o.row_end == -1 and o.force_path == -1
+    A = nat.spgemm_csr()
+    A.nrows, A.ncols, A.nnz = 10, 20, 0
+    A.row_ptr = 16  # never dereferenced by the size query
+    B = nat.spgemm_csr()
+    B.nrows, B.ncols, B.nnz = 20, 5, 0
+    B.row_ptr = 16
+    n = nat.spgemm_workspace_size(A, B, o)
+    assert n > 0
+    o.row_begin, o.row_end = 5, 3
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_workspace_size(A, B, o)
+    assert ei.value.status == 2
+    o = nat.spgemm_opts_default()
+    # dimension mismatch is caught on the host before any device work
+    A.ncols = 19
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_analyse(A, B, o, 256, 1 << 20, 0)
+    assert ei.value.status == 2
+    A.ncols = 20
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_analyse(A, B, o, 0, 0, 0)
+    assert ei.value.status == 5  # workspace missing
+    assert nat.spgemm_version().count(".") == 2
+    for s in range(10):
+        assert nat.spgemm_status_string(s)

@@ -1,0 +1,222 @@
+"""GPU parity of the single-product path (analyse -> symbolic -> scan ->
+numeric) against the CPU oracle, through the C ABI.
+
+Structure (row_ptr, col_idx, nnz) must match bit for bit; FP64 values within
+the criterion in parity.py, or bit for bit for integer-valued inputs (every
+partial sum is an exact integer below 2^53, so summation order is moot).
+"""
+import numpy as np
+import pytest
+
+from paper_2112_10037_gb300 import gen
+from parity import (RTOL_F32, assert_structure_equal, assert_values_close, assert_values_exact,
+                    oracle_with_scale, max_rel_err)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2112_10037_gb300 import build
+    build.build()
+    from paper_2112_10037_gb300 import api as a
+    return a
+
+
+def run(api, A, B, dtype=torch.float64, **kw):
+    dA = api.DeviceCSR.from_host(A, dtype=dtype)
+    dB = api.DeviceCSR.from_host(B, dtype=dtype)
+    plan = api.Plan(dA, dB, dtype=dtype, **kw)
+    rp, nnz = plan.symbolic()
+    ci, v = plan.numeric(dA.vals, dB.vals)
+    torch.cuda.synchronize()
+    plan.check()
+    stats = plan.stats()
+    plan.close()
+    C = gen.CSR(plan.nrows, B.ncols, rp.cpu().numpy(), ci.cpu().numpy(), v.double().cpu().numpy())
+    assert nnz == C.nnz
+    return C, stats
+
+
+PATHS = [-1, 1, 2, 3, 4]
+
+
+@pytest.mark.parametrize("force", PATHS)
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_small_all_paths(api, oracle_mod, force, seed):
+    A = gen.random_csr(300, 200, 0.05, seed, empty_rows=0.1)
+    B = gen.random_csr(200, 500, 0.08, seed + 50, empty_rows=0.1)
+    C, _ = run(api, A, B, force_path=force)
+    R, S = oracle_with_scale(oracle_mod, A, B)
+    assert_structure_equal(C, R)
+    assert_values_close(C.vals, R.vals, S)
+
+
+@pytest.mark.parametrize("force", PATHS)
+def test_integer_values_bit_exact(api, oracle_mod, force):
+    A = gen.random_csr(257, 301, 0.1, 7, values="int", empty_rows=0.15)
+    B = gen.random_csr(301, 263, 0.1, 8, values="int", empty_rows=0.15)
+    C, _ = run(api, A, B, force_path=force)
+    R = oracle_mod.spgemm(A, B)
+    assert_structure_equal(C, R)
+    assert_values_exact(C.vals, R.vals)
+
+
+@pytest.mark.parametrize("force", PATHS)
+def test_laplacian2d_64_squared(api, oracle_mod, force):
+    """The 64x64 2D 5-point Laplacian squared: bit-exact vs the oracle (and
+    hence vs the closed form the oracle is pinned to)."""
+    A = gen.laplacian_2d(64)
+    C, stats = run(api, A, A, force_path=force)
+    R = oracle_mod.spgemm(A, A)
+    assert C.nnz == 51972
+    assert_structure_equal(C, R)
+    assert_values_exact(C.vals, R.vals)
+    assert stats[0] == 100104
+
+
+@pytest.mark.parametrize("force", PATHS)
+def test_wide_rows_many_windows(api, oracle_mod, force):
+    """Long rows spanning many windows, hub-like B rows, ragged tails."""
+    rng = np.random.default_rng(3)
+    counts = rng.integers(0, 400, size=64)
+    counts[0] = 3000
+    A = gen.random_rows(64, 4000, counts, rng)
+    countsB = rng.integers(0, 60, size=4000)
+    countsB[:20] = 20000
+    B = gen.random_rows(4000, 70000, countsB, rng)
+    C, _ = run(api, A, B, force_path=force)
+    R, S = oracle_with_scale(oracle_mod, A, B)
+    assert_structure_equal(C, R)
+    assert_values_close(C.vals, R.vals, S)
+
+
+@pytest.mark.parametrize("P", [1, 7, 8, 9, 15, 16, 17, 31, 32, 33, 64, 65])
+def test_bin_boundaries(api, oracle_mod, P):
+    """Rows whose product count sits on each side of a bin edge."""
+    rng = np.random.default_rng(P)
+    B = gen.random_rows(P, 5000, np.ones(P, np.int64), rng)
+    A = gen.CSR(3, P, np.array([0, P, P, 2 * P], np.int32),
+                np.concatenate([np.arange(P), np.arange(P)]).astype(np.int32),
+                rng.standard_normal(2 * P))
+    C, _ = run(api, A, B)
+    R, S = oracle_with_scale(oracle_mod, A, B)
+    assert_structure_equal(C, R)
+    assert_values_close(C.vals, R.vals, S)
+
+
+def test_empty_and_degenerate(api, oracle_mod):
+    cases = [(0, 5, 7), (5, 0, 7), (5, 7, 0), (1, 1, 1)]
+    for (m, k, n) in cases:
+        A = gen.random_csr(m, k, 0.5, 1)
+        B = gen.random_csr(k, n, 0.5, 2)
+        C, _ = run(api, A, B)
+        R = oracle_mod.spgemm(A, B)
+        assert_structure_equal(C, R)
+        assert_values_exact(C.vals, R.vals)
+    # all rows empty
+    A = gen.CSR(10, 10, np.zeros(11, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    C, _ = run(api, A, gen.identity(10))
+    assert C.nnz == 0 and np.all(C.row_ptr == 0)
+
+
+def test_single_dense_row_and_identity(api, oracle_mod):
+    n = 20000
+    A = gen.CSR(1, n, np.array([0, n], np.int32), np.arange(n, dtype=np.int32), np.ones(n))
+    B = gen.random_csr(n, 300, 0.01, 5)
+    C, _ = run(api, A, B)
+    R, S = oracle_with_scale(oracle_mod, A, B)
+    assert_structure_equal(C, R)
+    assert_values_close(C.vals, R.vals, S)
+    M = gen.random_csr(500, 400, 0.02, 9)
+    C2, _ = run(api, gen.identity(500), M)
+    assert np.array_equal(C2.col_idx, M.col_idx) and np.array_equal(C2.vals, M.vals)
+
+
+def test_explicit_zeros_and_cancellation(api, oracle_mod):
+    A = gen.CSR(2, 3, np.array([0, 3, 5], np.int32), np.array([0, 1, 2, 0, 2], np.int32),
+                np.array([1.0, 1.0, 0.0, 2.0, -0.0]))
+    B = gen.CSR(3, 2, np.array([0, 2, 4, 6], np.int32), np.array([0, 1, 0, 1, 0, 1], np.int32),
+                np.array([2.0, 3.0, -2.0, 1.0, 5.0, 0.0]))
+    C, _ = run(api, A, B)
+    R = oracle_mod.spgemm(A, B)
+    assert_structure_equal(C, R)
+    assert np.array_equal(C.vals, R.vals)  # 0.0 == -0.0 is allowed here
+
+
+def test_row_range(api, oracle_mod):
+    A = gen.random_csr(400, 300, 0.05, 21)
+    B = gen.random_csr(300, 350, 0.05, 22)
+    C, _ = run(api, A, B, row_range=(123, 321))
+    R, S = oracle_with_scale(oracle_mod, oracle_mod.select_rows(A, np.arange(123, 321)), B)
+    assert_structure_equal(C, R)
+    assert_values_close(C.vals, R.vals, S)
+
+
+def test_numeric_repeat_new_values(api, oracle_mod):
+    A = gen.random_csr(200, 150, 0.06, 31)
+    B = gen.random_csr(150, 220, 0.06, 32)
+    dA = api.DeviceCSR.from_host(A)
+    dB = api.DeviceCSR.from_host(B)
+    plan = api.Plan(dA, dB)
+    rp, nnz = plan.symbolic()
+    for t in range(3):
+        rng = np.random.default_rng(100 + t)
+        A.vals = rng.standard_normal(A.nnz)
+        B.vals = rng.standard_normal(B.nnz)
+        ci, v = plan.numeric(torch.from_numpy(A.vals).cuda(), torch.from_numpy(B.vals).cuda())
+        C = gen.CSR(A.nrows, B.ncols, rp.cpu().numpy(), ci.cpu().numpy(), v.cpu().numpy())
+        R, S = oracle_with_scale(oracle_mod, A, B)
+        assert_structure_equal(C, R)
+        assert_values_close(C.vals, R.vals, S)
+    plan.close()
+
+
+@pytest.mark.parametrize("force", [-1, 3, 4])
+def test_fp32_values(api, oracle_mod, force):
+    A = gen.random_csr(300, 300, 0.05, 41)
+    B = gen.random_csr(300, 300, 0.05, 42)
+    C, _ = run(api, A, B, dtype=torch.float32, force_path=force)
+    A32 = A.astype(np.float32).astype(np.float64)
+    B32 = B.astype(np.float32).astype(np.float64)
+    A32 = gen.CSR(A.nrows, A.ncols, A.row_ptr, A.col_idx, A32.vals)
+    B32 = gen.CSR(B.nrows, B.ncols, B.row_ptr, B.col_idx, B32.vals)
+    R, S = oracle_with_scale(oracle_mod, A32, B32)
+    assert_structure_equal(C, R)
+    err = max_rel_err(C.vals, R.vals, S)
+    assert err <= RTOL_F32
+
+
+def test_validate_rejects_unsorted(api):
+    from paper_2112_10037_gb300._native import SpgemmError
+    A = gen.CSR(2, 3, np.array([0, 2, 3], np.int32), np.array([2, 1, 0], np.int32), np.ones(3))
+    B = gen.identity(3)
+    with pytest.raises(SpgemmError) as ei:
+        run(api, A, B, validate=True)
+    assert ei.value.status == 3
+    A2 = gen.CSR(2, 3, np.array([0, 2, 3], np.int32), np.array([0, 5, 0], np.int32), np.ones(3))
+    with pytest.raises(SpgemmError):
+        run(api, A2, B, validate=True)
+    # valid input passes validation
+    C, _ = run(api, gen.identity(3), B, validate=True)
+    assert C.nnz == 3
+
+
+def test_dim_mismatch(api):
+    from paper_2112_10037_gb300._native import SpgemmError
+    with pytest.raises(SpgemmError) as ei:
+        run(api, gen.random_csr(4, 5, 0.5, 1), gen.random_csr(6, 4, 0.5, 2))
+    assert ei.value.status == 2
+
+
+def test_rmat_scale14(api, oracle_mod):
+    A = gen.rmat(14, 16)
+    C, stats = run(api, A, A)
+    R, S = oracle_with_scale(oracle_mod, A, A)
+    assert_structure_equal(C, R)
+    assert_values_close(C.vals, R.vals, S)
+    assert stats[0] == int(oracle_mod.row_products(A, A).sum())
