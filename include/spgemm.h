@@ -82,11 +82,13 @@ typedef struct spgemm_opts {
                           3 (4) sends every non-empty row to the warp (block) path */
   int32_t hash_max;    /* rows of at most this many products use the shared-memory
                           hash accumulator (0: library default; -1: never) */
-  int32_t window_warp; /* accumulator width (columns) of the warp path, power of two
-                          in [256, 8192] (0: default) */
-  int32_t window_block;/* accumulator width of the block path, power of two in
-                          [1024, 16384] (0: default) */
-  int32_t reserved[7];
+  int32_t window_warp; /* columns of the numeric dense window (one per warp):
+                          1024, 2048 or 4096 (0: default 2048) */
+  int32_t window_block;/* reserved, keep 0 */
+  int32_t split_min;   /* rows with more products than this are split into column
+                          tiles of window_warp columns, processed independently
+                          (0: default 131072; -1: never split) */
+  int32_t reserved[6];
 } spgemm_opts;
 
 typedef struct spgemm_plan spgemm_plan;

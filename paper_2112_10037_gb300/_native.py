@@ -42,7 +42,8 @@ class spgemm_opts(ctypes.Structure):
                 ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64),
                 ("warp_max", ctypes.c_int32), ("force_path", ctypes.c_int32),
                 ("hash_max", ctypes.c_int32), ("window_warp", ctypes.c_int32),
-                ("window_block", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("window_block", ctypes.c_int32), ("split_min", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 _lib = None

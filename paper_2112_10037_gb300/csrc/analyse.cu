@@ -124,6 +124,46 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const long long* __restrict
   }
 }
 
+static int grid_for_warps(long long nwarps, int warps_per_block, int nsm);
+
+// First index of each coarse column tile in each row of B (one warp per
+// row): bnd[k][t] = first position of row k whose column is >= t * Tc, and
+// bnd[k][ntc] = end of the row.  Lets a split row find the part of B(k,:)
+// inside a tile without scanning from the row start.  Skipped when no row
+// is split.
+__global__ void __launch_bounds__(256) k_tile_bounds(Csr B, SplitInfo sp, const DevStats* st) {
+  __shared__ int s_any;
+  if (threadIdx.x == 0) s_any = split_rows(st, sp) > 0;
+  if (block_skip(st) || !s_any) return;
+  const int lane = lane_id();
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
+  const int stride = sp.ntc + 1;
+  for (long long k = w; k < B.nrows; k += nw) {
+    int32_t* bk = sp.bnd + k * stride;
+    const int rs = B.rp[k], re = B.rp[k + 1];
+    if (rs == re) {
+      for (int t = lane; t < stride; t += 32) bk[t] = rs;
+      continue;
+    }
+    if (lane == 0) bk[0] = rs;
+    for (int idx = rs + lane; idx < re; idx += 32) {
+      const int tcur = B.ci[idx] >> sp.tc_shift;
+      const int tprev = idx > rs ? (B.ci[idx - 1] >> sp.tc_shift) : 0;
+      for (int t = tprev + 1; t <= tcur && t <= sp.ntc; ++t) bk[t] = idx;
+      if (idx == re - 1)
+        for (int t = tcur + 1; t <= sp.ntc; ++t) bk[t] = re;
+    }
+  }
+}
+
+cudaError_t launch_tile_bounds(const LaunchCtx& c, const Csr& B, const SplitInfo& sp) {
+  if (sp.heavy_bin >= NBINS || B.nrows <= 0 || !sp.bnd) return cudaSuccess;
+  k_tile_bounds<<<grid_for_warps(B.nrows, 8, c.nsm), 256, 0, c.stream>>>(B, sp, c.st);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
 static int grid_for_warps(long long nwarps, int warps_per_block, int nsm) {
   long long blocks = (nwarps + warps_per_block - 1) / warps_per_block;
   long long cap = (long long)nsm * 8;

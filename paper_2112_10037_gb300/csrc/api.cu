@@ -21,10 +21,12 @@ struct spgemm_plan {
   int* cmax = nullptr;
   int* rows = nullptr;
   int32_t* cursor = nullptr;
+  int32_t* nxt = nullptr;
   long long* scan_part = nullptr;
   // host state
   sg::PathBins pb{};
   sg::Tuning tu{};
+  sg::SplitInfo sp{};
   bool symbolic_done = false;
   long long nnz_c = -1;
   int path_rows[sg::NPATHS] = {0, 0, 0, 0};
@@ -47,10 +49,50 @@ constexpr size_t ALIGN = 256;
 inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 
 struct Layout {
-  size_t st, prod, cmin, cmax, rows, cursor, scan, total;
+  size_t st, prod, cmin, cmax, rows, cursor, nxt, scan, bnd, hcnt, total;
 };
 
-Layout layout_for(long long mloc, long long nnz_a) {
+// Split geometry from the options and B's width (see sg::SplitInfo).
+void split_geometry(const spgemm_opts& o, int window, long long mloc, long long nrows_b, long long ncols_b,
+                    sg::SplitInfo* sp, size_t* bnd_entries, size_t* hcnt_entries) {
+  sp->heavy_bin = sg::NBINS;
+  sp->hcap = 0;
+  sp->wf_shift = 0;
+  while ((1 << sp->wf_shift) < window) ++sp->wf_shift;
+  sp->ntf = (int)((ncols_b + window - 1) / window);
+  long long tc = 8ll * window;
+  while ((ncols_b + tc - 1) / tc > 64) tc <<= 1;
+  sp->tc_shift = 0;
+  while ((1ll << sp->tc_shift) < tc) ++sp->tc_shift;
+  sp->ntc = (int)((ncols_b + tc - 1) / tc);
+  *bnd_entries = 0;
+  *hcnt_entries = 0;
+  if (o.split_min < 0 || o.force_path >= 0 || mloc <= 0 || sp->ntf < 2) return;
+  const long long smin = o.split_min > 0 ? o.split_min : 131072;
+  const size_t bnd = (size_t)nrows_b * (size_t)(sp->ntc + 1);
+  if (bnd > (size_t)1 << 28) return;  // table would be too large: never split
+  long long cap = mloc < 16384 ? mloc : 16384;
+  const long long lim = ((long long)1 << 24) / sp->ntf;
+  if (cap > lim) cap = lim;
+  if (cap <= 0) return;
+  // split rows always lie above the register-sort bins (1..8), so their
+  // sizes come from the bitmap-window kernel, which records per-tile counts
+  sp->heavy_bin = sg::bin_of(smin) + 1;
+  if (sp->heavy_bin < 9) sp->heavy_bin = 9;
+  if (sp->heavy_bin >= sg::NBINS) { sp->heavy_bin = sg::NBINS; return; }
+  sp->hcap = (int)cap;
+  *bnd_entries = bnd;
+  *hcnt_entries = (size_t)cap * (size_t)sp->ntf;
+}
+
+int numeric_window(const spgemm_opts& o) {
+  return (o.window_warp == 1024 || o.window_warp == 4096) ? o.window_warp : 2048;
+}
+
+Layout layout_for(const spgemm_opts& o, long long mloc, long long nnz_a, long long nrows_b, long long ncols_b) {
+  sg::SplitInfo sp;
+  size_t nb = 0, nh = 0;
+  split_geometry(o, numeric_window(o), mloc, nrows_b, ncols_b, &sp, &nb, &nh);
   Layout L{};
   size_t off = 0;
   L.st = off; off = align_up(off + sizeof(sg::DevStats));
@@ -59,7 +101,10 @@ Layout layout_for(long long mloc, long long nnz_a) {
   L.cmax = off; off = align_up(off + sizeof(int) * (size_t)mloc);
   L.rows = off; off = align_up(off + sizeof(int) * (size_t)mloc);
   L.cursor = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
+  L.nxt = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
   L.scan = off; off = align_up(off + sizeof(long long) * sg::scan_partials_count(mloc));
+  L.bnd = off; off = align_up(off + sizeof(int32_t) * nb);
+  L.hcnt = off; off = align_up(off + sizeof(int32_t) * nh);
   L.total = off;
   return L;
 }
@@ -86,29 +131,24 @@ spgemm_status check_csr(const spgemm_csr* M) {
   return SPGEMM_OK;
 }
 
-int pow2_at_least(int v, int lo, int hi) {
-  int p = lo;
-  while (p < v && p < hi) p <<= 1;
-  return p;
-}
-
 // Bin ranges of the paths from the options (see sg::bin_of for the bins).
 void choose_paths(const spgemm_opts& o, sg::PathBins* pb, sg::Tuning* tu) {
   const int last = sg::NBINS - 1;
   tu->warp_max = o.warp_max > 0 ? o.warp_max : 8192;
-  tu->window_warp = o.window_warp > 0 ? pow2_at_least(o.window_warp, 512, 2048) : 1024;
-  tu->window_block = o.window_block > 0 ? pow2_at_least(o.window_block, 4096, 16384) : 8192;
+  tu->window_warp = numeric_window(o);
+  tu->window_block = 0;
   tu->hash_max = 0;
-  const int wb = sg::bin_of(tu->warp_max) < 7 ? 7 : sg::bin_of(tu->warp_max);
+  constexpr int TINY_HI = 8;  // register sort up to 128 products
+  const int wb = sg::bin_of(tu->warp_max) < TINY_HI + 1 ? TINY_HI + 1 : sg::bin_of(tu->warp_max);
   for (int p = 0; p < sg::NPATHS; ++p) { pb->lo[p] = 1; pb->hi[p] = 0; }
   switch (o.force_path) {
-    case 1: pb->lo[sg::PATH_TINY] = 1; pb->hi[sg::PATH_TINY] = 6; pb->lo[sg::PATH_WARP] = 7; pb->hi[sg::PATH_WARP] = last; break;
-    case 2: pb->lo[sg::PATH_TINY] = 1; pb->hi[sg::PATH_TINY] = 6; pb->lo[sg::PATH_BLOCK] = 7; pb->hi[sg::PATH_BLOCK] = last; break;
+    case 1: pb->lo[sg::PATH_TINY] = 1; pb->hi[sg::PATH_TINY] = TINY_HI; pb->lo[sg::PATH_WARP] = TINY_HI + 1; pb->hi[sg::PATH_WARP] = last; break;
+    case 2: pb->lo[sg::PATH_TINY] = 1; pb->hi[sg::PATH_TINY] = TINY_HI; pb->lo[sg::PATH_BLOCK] = TINY_HI + 1; pb->hi[sg::PATH_BLOCK] = last; break;
     case 3: pb->lo[sg::PATH_WARP] = 1; pb->hi[sg::PATH_WARP] = last; break;
     case 4: pb->lo[sg::PATH_BLOCK] = 1; pb->hi[sg::PATH_BLOCK] = last; break;
     default:
-      pb->lo[sg::PATH_TINY] = 1; pb->hi[sg::PATH_TINY] = 6;
-      pb->lo[sg::PATH_WARP] = 7; pb->hi[sg::PATH_WARP] = wb;
+      pb->lo[sg::PATH_TINY] = 1; pb->hi[sg::PATH_TINY] = TINY_HI;
+      pb->lo[sg::PATH_WARP] = TINY_HI + 1; pb->hi[sg::PATH_WARP] = wb;
       pb->lo[sg::PATH_BLOCK] = wb + 1; pb->hi[sg::PATH_BLOCK] = last;
       break;
   }
@@ -173,6 +213,7 @@ void spgemm_opts_default(spgemm_opts* o) {
   o->hash_max = 0;
   o->window_warp = 0;
   o->window_block = 0;
+  o->split_min = 0;
 }
 
 const char* spgemm_status_string(spgemm_status s) {
@@ -203,7 +244,7 @@ spgemm_status spgemm_workspace_size(const spgemm_csr* A, const spgemm_csr* B, co
   if (opts) o = *opts; else spgemm_opts_default(&o);
   const long long rb = o.row_begin, re = o.row_end < 0 ? A->nrows : o.row_end;
   if (rb < 0 || re < rb || re > A->nrows) return SPGEMM_ERR_DIM_MISMATCH;
-  *bytes = layout_for(re - rb, A->nnz).total;
+  *bytes = layout_for(o, re - rb, A->nnz, B->nrows, B->ncols).total;
   return SPGEMM_OK;
 }
 
@@ -222,7 +263,7 @@ spgemm_status spgemm_analyse(const spgemm_csr* A, const spgemm_csr* B, const spg
   if (o.force_path < -1 || o.force_path > 4) return SPGEMM_ERR_INVALID_ARG;
   const long long rb = o.row_begin, re = o.row_end < 0 ? A->nrows : o.row_end;
   if (rb < 0 || re < rb || re > A->nrows) return SPGEMM_ERR_DIM_MISMATCH;
-  const Layout L = layout_for(re - rb, A->nnz);
+  const Layout L = layout_for(o, re - rb, A->nnz, B->nrows, B->ncols);
   if (!workspace || workspace_bytes < L.total) return SPGEMM_ERR_WORKSPACE;
   if (((uintptr_t)workspace) % 16) return SPGEMM_ERR_WORKSPACE;
 
@@ -244,8 +285,15 @@ spgemm_status spgemm_analyse(const spgemm_csr* A, const spgemm_csr* B, const spg
   p->cmax = (int*)(p->ws + L.cmax);
   p->rows = (int*)(p->ws + L.rows);
   p->cursor = (int32_t*)(p->ws + L.cursor);
+  p->nxt = (int32_t*)(p->ws + L.nxt);
   p->scan_part = (long long*)(p->ws + L.scan);
   choose_paths(o, &p->pb, &p->tu);
+  {
+    size_t nb = 0, nh = 0;
+    split_geometry(o, p->tu.window_warp, p->mloc, B->nrows, B->ncols, &p->sp, &nb, &nh);
+    p->sp.bnd = nb ? (int32_t*)(p->ws + L.bnd) : nullptr;
+    p->sp.hcnt = nh ? (int32_t*)(p->ws + L.hcnt) : nullptr;
+  }
 
   cudaStream_t st = (cudaStream_t)stream;
   sg::LaunchCtx c = ctx_of(p, stream);
@@ -255,6 +303,7 @@ spgemm_status spgemm_analyse(const spgemm_csr* A, const spgemm_csr* B, const spg
     if (e == cudaSuccess) e = sg::launch_validate(c, p->B);
   }
   if (e == cudaSuccess) e = sg::launch_analyse(c, p->A, p->B, p->row_begin, p->mloc, p->prod, p->cmin, p->cmax, p->rows);
+  if (e == cudaSuccess) e = sg::launch_tile_bounds(c, p->B, p->sp);
   if (e != cudaSuccess) { delete p; return SPGEMM_ERR_CUDA; }
   *plan = p;
   return SPGEMM_OK;
@@ -267,7 +316,7 @@ spgemm_status spgemm_symbolic(spgemm_plan* p, int32_t* c_row_ptr, int64_t* c_nnz
   const sg::RowInfo ri = rowinfo_of(p);
   cudaError_t e = cudaMemsetAsync(c_row_ptr, 0, sizeof(int32_t) * (size_t)(p->mloc + 1), st);
   if (e == cudaSuccess && p->mloc > 0)
-    e = sg::launch_symbolic(c, p->A, p->B, ri, p->pb, p->tu, p->cursor, c_row_ptr, nullptr);
+    e = sg::launch_symbolic(c, p->A, p->B, ri, p->pb, p->tu, p->sp, p->cursor, c_row_ptr, nullptr);
   if (e == cudaSuccess) e = sg::launch_scan(c, c_row_ptr, p->mloc, p->scan_part);
   if (e != cudaSuccess) return SPGEMM_ERR_CUDA;
   spgemm_status s = read_stats(p, st);
@@ -289,8 +338,8 @@ spgemm_status spgemm_numeric(spgemm_plan* p, const void* a_vals, const void* b_v
   if (!a_vals || !b_vals || !c_col_idx || !c_vals) return SPGEMM_ERR_INVALID_ARG;
   sg::LaunchCtx c = ctx_of(p, stream);
   const sg::RowInfo ri = rowinfo_of(p);
-  cudaError_t e = sg::launch_numeric(c, p->A, p->B, ri, p->pb, p->tu, p->opts.dtype, a_vals, b_vals, p->cursor,
-                                     c_row_ptr, c_col_idx, c_vals, p->path_rows);
+  cudaError_t e = sg::launch_numeric(c, p->A, p->B, ri, p->pb, p->tu, p->sp, p->opts.dtype, a_vals, b_vals,
+                                     p->cursor, p->nxt, c_row_ptr, c_col_idx, c_vals, p->path_rows);
   return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 

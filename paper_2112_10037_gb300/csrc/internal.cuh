@@ -76,12 +76,27 @@ struct PathBins {
   int hi[NPATHS];  // inclusive; hi < lo means the path is unused
 };
 
-// Window widths (columns) of the dense-window accumulators.
+// Tuning of the paths, fixed when the plan is made.
 struct Tuning {
-  int window_warp;     // numeric, one warp per row
-  int window_block;    // numeric, one block per row
+  int window_warp;     // numeric window width (columns) of the warp accumulator
+  int window_block;    // unused by the numeric pass (kept for the option)
   int hash_max;        // largest P of the hash path (0: path disabled)
-  int warp_max;        // largest P of the warp path
+  int warp_max;        // largest P of the symbolic warp path
+};
+
+// Splitting of heavy rows into column tiles (numeric pass) and the tables
+// the split needs.  Heavy rows are the leading rows of the descending-bin
+// list whose bin is >= heavy_bin, at most hcap of them; row h of the list
+// owns hcnt[h * ntf .. h * ntf + ntf).
+struct SplitInfo {
+  int heavy_bin;      // NBINS disables splitting
+  int hcap;
+  int wf_shift;       // log2 of the fine tile width (= numeric window)
+  int ntf;            // fine tiles per row: ceil(ncols(B) / fine width)
+  int tc_shift;       // log2 of the coarse tile width
+  int ntc;            // coarse tiles per row: ceil(ncols(B) / coarse width)
+  int32_t* bnd;       // nrows(B) x (ntc + 1): first index of each coarse tile in each B row
+  int32_t* hcnt;      // hcap x ntf output counts
 };
 
 // ---------------------------------------------------------------- warp utils
@@ -190,15 +205,26 @@ inline void count_launch(const LaunchCtx& c) {
 cudaError_t launch_validate(const LaunchCtx& c, const Csr& M);
 cudaError_t launch_analyse(const LaunchCtx& c, const Csr& A, const Csr& B, long long row_begin,
                            long long mloc, long long* prod, int* cmin, int* cmax, int* rows);
+cudaError_t launch_tile_bounds(const LaunchCtx& c, const Csr& B, const SplitInfo& sp);
 cudaError_t launch_symbolic(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
-                            const PathBins& pb, const Tuning& tu, int32_t* cursor,
+                            const PathBins& pb, const Tuning& tu, const SplitInfo& sp, int32_t* cursor,
                             int32_t* c_rp, const int* path_rows /* host, may be null */);
 cudaError_t launch_scan(const LaunchCtx& c, int32_t* c_rp, long long mloc, long long* partials);
 size_t scan_partials_count(long long mloc);
 cudaError_t launch_numeric(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
-                           const PathBins& pb, const Tuning& tu, int dtype, const void* av,
-                           const void* bv, int32_t* cursor, const int32_t* c_rp, int32_t* c_ci,
-                           void* c_v, const int* path_rows /* host, may be null */);
+                           const PathBins& pb, const Tuning& tu, const SplitInfo& sp, int dtype,
+                           const void* av, const void* bv, int32_t* cursor, int32_t* nxt,
+                           const int32_t* c_rp, int32_t* c_ci, void* c_v,
+                           const int* path_rows /* host, may be null */);
+
+// Number of split (heavy) rows: the leading rows of bins >= heavy_bin,
+// capped at hcap.
+__device__ __forceinline__ int split_rows(const DevStats* st, const SplitInfo& sp) {
+  if (sp.heavy_bin >= NBINS) return 0;
+  int n = 0;
+  for (int b = sp.heavy_bin; b < NBINS; ++b) n += st->hist[b];
+  return n < sp.hcap ? n : sp.hcap;
+}
 
 
 }  // namespace sg

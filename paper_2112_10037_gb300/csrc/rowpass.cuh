@@ -6,20 +6,20 @@
 //
 // Two accumulators are used, chosen per row by its product count P:
 //
-//  * register sort (P <= 32): a group of G lanes holds one product per lane,
-//    sorts the (column, value) pairs with a bitonic network over shuffles
-//    and adds runs of equal columns with a segmented suffix sum.  The sorted
-//    order is the output order, so nothing is written to shared memory.
+//  * register sort (P <= 128): a group of G lanes holds up to E products per
+//    lane, sorts the (column, value) pairs with a bitonic network over
+//    shuffles and registers, and adds runs of equal columns with a segmented
+//    suffix sum.  The sorted order is the output order, so nothing is
+//    written to shared memory.
 //
-//  * dense column window: a warp (or a block) owns a window of W
-//    consecutive columns held as a presence bitmap plus, for the numeric
-//    pass, a dense value array in shared memory.  Every B row touched by the
-//    row is read from a per-nonzero cursor up to the window's end (rows of
-//    B are sorted, so that is one contiguous segment), products are added
-//    with shared-memory atomics, and the window is emitted in column order
-//    by a popcount prefix over the bitmap -- no sort is needed.  The next
+//  * bitmap window (symbolic pass, larger rows): a warp or a block owns a
+//    presence bitmap of W consecutive columns in shared memory.  Every B
+//    row touched by the row is read from a per-nonzero cursor up to the
+//    window's end (rows of B are sorted, so that is one contiguous segment)
+//    and sets one bit per product; the row size is the popcount.  The next
 //    window starts at the smallest column still unread, so windows skip
-//    column ranges the row does not touch.
+//    column ranges the row does not touch.  The numeric counterpart (a dense
+//    value window per warp) is in numwarp.cuh.
 #pragma once
 
 #include "internal.cuh"
@@ -27,13 +27,19 @@
 namespace sg {
 
 // ---------------------------------------------------------------- tiny path
-// One row per group of G lanes (G in 8/16/32), P <= G products.
-template <int G, bool NUM, typename T>
+// One row per group of G lanes holding E products per lane (G*E >= P).
+// Element x of the row's product sequence lives in slot x / G of lane x % G,
+// so every slot is a run of G consecutive elements after the sort; the
+// bitonic network exchanges through shuffles (partner distance < G) or
+// between a lane's own slots (distance >= G).
+template <int G, int E, bool NUM, typename T>
 __global__ void __launch_bounds__(256)
 k_tiny(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri,
        const DevStats* st, int bin_lo, int bin_hi, int32_t* __restrict__ c_cnt,
        const int32_t* __restrict__ c_rp, int32_t* __restrict__ c_ci, T* __restrict__ c_v,
        uint32_t* err) {
+  static_assert(E == 1 || G == 32, "multi-slot rows use whole warps");
+  constexpr int N = G * E;
   __shared__ int s_lb, s_le;
   if (threadIdx.x == 0) bin_range(st, bin_lo, bin_hi, &s_lb, &s_le);
   if (block_skip(st)) return;
@@ -55,18 +61,20 @@ k_tiny(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo
       a0 = A.rp[i];
       a1 = A.rp[i + 1];
     }
-    // Gather: lane gl of the group takes the row's gl-th product.
-    int col = INT_MAX;
-    T val = T(0);
+    // Gather: slot s of lane gl takes the row's (s*G + gl)-th product.
+    int col[E];
+    T val[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) { col[s] = INT_MAX; val[s] = T(0); }
     int done = 0;
     for (int e0 = a0; __any_sync(FULL, e0 < a1); e0 += G) {
       const int e = e0 + gl;
-      int s = 0, len = 0;
+      int sb = 0, len = 0;
       T a = T(0);
       if (e < a1) {
         const int k = A.ci[e];
-        s = B.rp[k];
-        len = B.rp[k + 1] - s;
+        sb = B.rp[k];
+        len = B.rp[k + 1] - sb;
         if (NUM) a = av[e];
       }
       int incl = len;
@@ -76,74 +84,133 @@ k_tiny(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo
         if (gl >= d) incl += t;
       }
       const int tot = __shfl_sync(FULL, incl, G - 1, G);
-      const int q = gl - done;
-      int o = 0;
+      const int excl = incl - len;
 #pragma unroll
-      for (int sp = G / 2; sp >= 1; sp >>= 1) {
-        const int t = __shfl_sync(FULL, incl, o + sp - 1, G);
-        if (t <= q) o += sp;
-      }
-      const int os = __shfl_sync(FULL, s, o, G);
-      const int oex = __shfl_sync(FULL, incl - len, o, G);
-      const T oa = __shfl_sync(FULL, a, o, G);
-      if (q >= 0 && q < tot) {
-        const int bi = os + q - oex;
-        col = B.ci[bi];
-        if (NUM) val = oa * bv[bi];
+      for (int s = 0; s < E; ++s) {
+        const int q = s * G + gl - done;
+        int o = 0;
+#pragma unroll
+        for (int sp = G / 2; sp >= 1; sp >>= 1) {
+          const int t = __shfl_sync(FULL, incl, o + sp - 1, G);
+          if (t <= q) o += sp;
+        }
+        const int os = __shfl_sync(FULL, sb, o, G);
+        const int oex = __shfl_sync(FULL, excl, o, G);
+        const T oa = __shfl_sync(FULL, a, o, G);
+        if (q >= 0 && q < tot) {
+          const int bi = os + q - oex;
+          col[s] = B.ci[bi];
+          if (NUM) val[s] = oa * bv[bi];
+        }
       }
       done += tot;
     }
-    if (!NUM) {
+    if (!NUM && E == 1) {
       // Distinct columns: one leader per run of equal keys inside the group.
-      const unsigned long long key = ((unsigned long long)(unsigned)gi << 32) | (unsigned)col;
+      const unsigned long long key = ((unsigned long long)(unsigned)gi << 32) | (unsigned)col[0];
       const unsigned m = __match_any_sync(FULL, key);
-      const bool leader = col != INT_MAX && (__ffs(m) - 1) == lane;
+      const bool leader = col[0] != INT_MAX && (__ffs(m) - 1) == lane;
       const int cnt = __popc(__ballot_sync(FULL, leader) & gmask);
       if (vrow && gl == 0) c_cnt[r] = cnt;
-    } else {
-      // Bitonic sort of (col, val) by col inside the group.
+      continue;
+    }
+    // Bitonic sort of the N = G*E elements by column.
 #pragma unroll
-      for (int k = 2; k <= G; k <<= 1) {
+    for (int k = 2; k <= N; k <<= 1) {
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-          const int pc = __shfl_xor_sync(FULL, col, j);
-          const T pv = __shfl_xor_sync(FULL, val, j);
-          const bool up = (gl & k) == 0;
-          const bool lower = (gl & j) == 0;
-          const bool take = (lower == up) ? (pc < col) : (pc > col);
-          if (take) {
-            col = pc;
-            val = pv;
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        if (j >= G) {
+#pragma unroll
+          for (int s = 0; s < E; ++s) {
+            const int s2 = s ^ (j / G);
+            if (s < s2) {
+              const bool up = ((s * G + gl) & k) == 0;
+              if (up ? (col[s] > col[s2]) : (col[s] < col[s2])) {
+                const int tc = col[s]; col[s] = col[s2]; col[s2] = tc;
+                if (NUM) { const T tv = val[s]; val[s] = val[s2]; val[s2] = tv; }
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int s = 0; s < E; ++s) {
+            const int pc = __shfl_xor_sync(FULL, col[s], j);
+            T pv = T(0);
+            if (NUM) pv = __shfl_xor_sync(FULL, val[s], j);
+            const bool up = ((s * G + gl) & k) == 0;
+            const bool lower = (gl & j) == 0;
+            const bool take = (lower == up) ? (pc < col[s]) : (pc > col[s]);
+            if (take) {
+              col[s] = pc;
+              if (NUM) val[s] = pv;
+            }
           }
         }
       }
-      // Segmented suffix sum over runs of equal columns.
-      T acc = val;
+    }
+    // Heads of runs of equal columns, in element order.
+    bool head[E];
+    int nheads = 0;
+    unsigned hb[E];
+#pragma unroll
+    for (int s = 0; s < E; ++s) {
+      // every lane executes both shuffles (s is a compile-time constant)
+      const int up1 = __shfl_up_sync(FULL, col[s], 1, G);
+      const int prevlast = (s > 0) ? __shfl_sync(FULL, col[s > 0 ? s - 1 : 0], G - 1, G) : -1;
+      const int prev = (gl == 0) ? prevlast : up1;
+      head[s] = col[s] != INT_MAX && prev != col[s];
+      hb[s] = __ballot_sync(FULL, head[s]) & gmask;
+      nheads += __popc(hb[s]);
+    }
+    if (!NUM) {
+      if (vrow && gl == 0) c_cnt[r] = nheads;
+      continue;
+    }
+    // Segmented suffix sums, last slot first, carrying runs across slots.
+    T acc[E];
+#pragma unroll
+    for (int s = E - 1; s >= 0; --s) {
+      T a = val[s];
 #pragma unroll
       for (int d = 1; d < G; d <<= 1) {
-        const T t = __shfl_down_sync(FULL, acc, d, G);
-        const int tc = __shfl_down_sync(FULL, col, d, G);
-        if (gl + d < G && tc == col) acc += t;
+        const T t = __shfl_down_sync(FULL, a, d, G);
+        const int tc = __shfl_down_sync(FULL, col[s], d, G);
+        if (gl + d < G && tc == col[s]) a += t;
       }
-      const int prevc = __shfl_up_sync(FULL, col, 1, G);
-      const bool head = col != INT_MAX && (gl == 0 || prevc != col);
-      const unsigned hb = __ballot_sync(FULL, head) & gmask;
-      if (vrow) {
-        const long long ob = c_rp[r], oe = c_rp[r + 1];
-        if (head) {
-          const long long o = ob + __popc(hb & lanemask_lt());
+      if (s < E - 1) {
+        const int lastc = __shfl_sync(FULL, col[s], G - 1, G);
+        const int nextc = __shfl_sync(FULL, col[s < E - 1 ? s + 1 : s], 0, G);
+        const T nexta = __shfl_sync(FULL, acc[s < E - 1 ? s + 1 : s], 0, G);
+        if (nextc == lastc && col[s] == lastc) a += nexta;
+      }
+      acc[s] = a;
+    }
+    if (vrow) {
+      const long long ob = c_rp[r], oe = c_rp[r + 1];
+      long long before = 0;
+#pragma unroll
+      for (int s = 0; s < E; ++s) {
+        if (head[s]) {
+          const long long o = ob + before + __popc(hb[s] & lanemask_lt());
           if (o < oe) {
-            c_ci[o] = col;
-            c_v[o] = acc;
+            c_ci[o] = col[s];
+            c_v[o] = acc[s];
           }
         }
-        if (gl == 0 && ob + __popc(hb) != oe) atomicOr(err, EB_INTERNAL);
+        before += __popc(hb[s]);
       }
+      if (gl == 0 && ob + nheads != oe) atomicOr(err, EB_INTERNAL);
     }
   }
 }
 
-// ------------------------------------------------------- dense-window path
+// ------------------------------------------------------- bitmap-window path
+// Symbolic pass for rows above the register-sort limit: a group of GW warps
+// owns a presence bitmap of W columns; each product sets its column's bit
+// (shared-memory atomicOr after a plain test), and the row size is the
+// popcount of the window.  Windows start at a multiple of 32 at or below the
+// smallest unread column.  For split rows the popcounts are also added up
+// per fine tile into hcnt, which fixes where each tile's entries go.
 template <int GW>
 __device__ __forceinline__ void group_sync(int g) {
   if (GW == 1) {
@@ -153,71 +220,70 @@ __device__ __forceinline__ void group_sync(int g) {
   }
 }
 
-template <int W, bool NUM, typename T>
-__device__ __forceinline__ void win_insert(T* acc, uint32_t* bits, int j, T v, uint32_t* err) {
+__device__ __forceinline__ void bit_insert(uint32_t* bits, int j, int W, uint32_t* err) {
   if ((unsigned)j >= (unsigned)W) {  // only reachable with unsorted input
     atomicOr(err, EB_UNSORTED);
     return;
   }
   const uint32_t m = 1u << (j & 31);
-  if (NUM) {
-    atomicAdd(&acc[j], v);
-    atomicOr(&bits[j >> 5], m);
-  } else {
-    if (!(bits[j >> 5] & m)) atomicOr(&bits[j >> 5], m);
-  }
+  if (!(bits[j >> 5] & m)) atomicOr(&bits[j >> 5], m);
 }
 
-template <int W, bool NUM, typename T>
-constexpr size_t window_group_bytes(int gw) {
-  return (((NUM ? (size_t)W * sizeof(T) : 0) + (size_t)(W / 32) * 4 + (size_t)gw * 8) + 15) & ~(size_t)15;
+// Smallest fine-tile width the symbolic kernel sizes its tile counters for.
+constexpr int SYM_MIN_FINE = 1024;
+
+template <int W, int GW, int WF = SYM_MIN_FINE>
+constexpr size_t sym_group_bytes() {
+  return (((size_t)(W / 32) * 4 + (size_t)GW * 8 + (size_t)(W / WF + 2) * 4) + 15) & ~(size_t)15;
 }
 
-// GW warps per row (group), CW warps per block, W columns per window.
-template <int GW, int CW, int W, bool NUM, typename T>
+// GW warps per row (group), CW warps per block, W columns per window; the
+// fine tile width is 2^sp.wf_shift >= SYM_MIN_FINE columns.
+template <int GW, int CW, int W>
 __global__ void __launch_bounds__(CW * 32)
-k_window(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri,
-         const DevStats* st, int bin_lo, int bin_hi, int32_t* __restrict__ cursor,
-         int32_t* __restrict__ c_cnt, const int32_t* __restrict__ c_rp, int32_t* __restrict__ c_ci,
-         T* __restrict__ c_v, uint32_t* err) {
+k_sym_window(Csr A, Csr B, RowInfo ri, const DevStats* st, int bin_lo, int bin_hi, SplitInfo sp,
+             int32_t* __restrict__ cursor, int32_t* __restrict__ c_cnt, uint32_t* err) {
   static_assert(CW % GW == 0 && W % 32 == 0, "bad shape");
   constexpr int NWORDS = W / 32;
   constexpr int NG = CW / GW;
-  constexpr size_t ACC_BYTES = NUM ? (size_t)W * sizeof(T) : 0;
-  constexpr size_t GB = window_group_bytes<W, NUM, T>(GW);
+  constexpr int NTW = W / SYM_MIN_FINE + 2;  // fine tiles a window can touch
+  constexpr size_t GB = sym_group_bytes<W, GW>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_lb, s_le;
+  __shared__ int s_lb, s_le, s_nh;
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const int g = warp / GW, wig = warp % GW;
   unsigned char* gbase = smem_raw + (size_t)g * GB;
-  T* acc = reinterpret_cast<T*>(gbase);
-  uint32_t* bits = reinterpret_cast<uint32_t*>(gbase + ACC_BYTES);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(gbase);
   int* wcnt = reinterpret_cast<int*>(bits + NWORDS);
   int* wnext = wcnt + GW;
+  int* tcnt = wnext + GW;
   for (int t = wig * 32 + lane; t < NWORDS; t += GW * 32) bits[t] = 0u;
-  if (NUM)
-    for (int t = wig * 32 + lane; t < W; t += GW * 32) acc[t] = T(0);
-  if (threadIdx.x == 0) bin_range(st, bin_lo, bin_hi, &s_lb, &s_le);
+  for (int t = wig * 32 + lane; t < NTW; t += GW * 32) tcnt[t] = 0;
+  if (threadIdx.x == 0) {
+    bin_range(st, bin_lo, bin_hi, &s_lb, &s_le);
+    s_nh = split_rows(st, sp);
+  }
   if (block_skip(st)) return;
-  const int lb = s_lb, le = s_le;
+  const int lb = s_lb, le = s_le, nh = s_nh;
+  const int wf_shift = sp.wf_shift;
 
   for (long long idx = lb + (long long)blockIdx.x * NG + g; idx < le; idx += (long long)gridDim.x * NG) {
     const int r = ri.rows[idx];
+    const bool split = idx < nh;
     const long long i = ri.row_begin + r;
     const int a0 = A.rp[i], a1 = A.rp[i + 1], nA = a1 - a0;
-    int base = ri.cmin[r];
+    int base = ri.cmin[r] & ~31;
     const int last = ri.cmax[r];
     const int CS = min(32, max(1, (nA + GW - 1) / GW));  // nonzeros per chunk
     const int nch = (nA + CS - 1) / CS;
     const bool regcur = nch <= GW;  // one chunk per warp: cursor stays in a register
     int rcur = 0;
-    long long obeg = 0, oend = 0;
-    if (NUM) {
-      obeg = c_rp[r];
-      oend = c_rp[r + 1];
-    }
     long long rowcount = 0;
     bool first = true;
+    if (split) {
+      for (int t = wig * 32 + lane; t < sp.ntf; t += GW * 32) sp.hcnt[(size_t)idx * sp.ntf + t] = 0;
+      group_sync<GW>(g);
+    }
     while (true) {
       const int wend = (int)min((long long)base + W, (long long)INT_MAX);
       int mynext = INT_MAX;
@@ -225,10 +291,8 @@ k_window(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowIn
         const int e = a0 + c * CS + lane;
         const bool ve = lane < CS && e < a1;
         int s = 0, len = 0;
-        T a = T(0);
         if (ve) {
           const int k = A.ci[e];
-          if (NUM) a = av[e];
           const int rs = B.rp[k], re = B.rp[k + 1];
           const int cur = first ? rs : (regcur ? rcur : cursor[e]);
           int seg = cur, nx = INT_MAX;
@@ -256,26 +320,30 @@ k_window(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowIn
           const int L = __ffs(lm) - 1;
           lm &= lm - 1;
           const int ls = __shfl_sync(FULL, s, L), ln = __shfl_sync(FULL, len, L);
-          const T la = __shfl_sync(FULL, a, L);
-          for (int t = lane; t < ln; t += 32) {
-            const int bi = ls + t;
-            win_insert<W, NUM, T>(acc, bits, B.ci[bi] - base, NUM ? la * bv[bi] : T(0), err);
+          int t = lane;
+          for (; t + 96 < ln; t += 128) {
+            const int c0 = B.ci[ls + t], c1 = B.ci[ls + t + 32], c2 = B.ci[ls + t + 64], c3 = B.ci[ls + t + 96];
+            bit_insert(bits, c0 - base, W, err);
+            bit_insert(bits, c1 - base, W, err);
+            bit_insert(bits, c2 - base, W, err);
+            bit_insert(bits, c3 - base, W, err);
           }
+          for (; t < ln; t += 32) bit_insert(bits, B.ci[ls + t] - base, W, err);
         }
         // Short segments: flattened so every lane takes one product.
         const int sl = len < 32 ? len : 0;
         const int incl = warp_incl_scan(sl);
         const int tot = __shfl_sync(FULL, incl, 31);
-        for (int p0 = 0; p0 < tot; p0 += 32) {
-          const int p = p0 + lane;
-          const int o = warp_owner(incl, p);
-          const int os = __shfl_sync(FULL, s, o);
-          const int oex = __shfl_sync(FULL, incl - sl, o);
-          const T oa = __shfl_sync(FULL, a, o);
-          if (p < tot) {
-            const int bi = os + p - oex;
-            win_insert<W, NUM, T>(acc, bits, B.ci[bi] - base, NUM ? oa * bv[bi] : T(0), err);
-          }
+        const int excl = incl - sl;
+        for (int p0 = 0; p0 < tot; p0 += 64) {
+          const int p = p0 + lane, p2 = p + 32;
+          const int o = warp_owner(incl, p), o2 = warp_owner(incl, p2);
+          const int os = __shfl_sync(FULL, s, o), oex = __shfl_sync(FULL, excl, o);
+          const int os2 = __shfl_sync(FULL, s, o2), oex2 = __shfl_sync(FULL, excl, o2);
+          const int c0 = p < tot ? B.ci[os + p - oex] : 0;
+          const int c1 = p2 < tot ? B.ci[os2 + p2 - oex2] : 0;
+          if (p < tot) bit_insert(bits, c0 - base, W, err);
+          if (p2 < tot) bit_insert(bits, c1 - base, W, err);
         }
       }
       mynext = warp_min(mynext);
@@ -284,10 +352,13 @@ k_window(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowIn
       group_sync<GW>(g);
       const int wpw = (nw + GW - 1) / GW;
       const int w0 = min(nw, wig * wpw), w1 = min(nw, w0 + wpw);
+      const int tile0 = base >> wf_shift;
       int cnt = 0;
       for (int j = w0 + lane; j < w1; j += 32) {
-        cnt += __popc(bits[j]);
-        if (!NUM) bits[j] = 0u;
+        const int pc = __popc(bits[j]);
+        bits[j] = 0u;
+        cnt += pc;
+        if (split && pc) atomicAdd(&tcnt[((base + 32 * j) >> wf_shift) - tile0], pc);
       }
       cnt = warp_sum(cnt);
       if (lane == 0) {
@@ -295,54 +366,18 @@ k_window(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowIn
         wnext[wig] = mynext;
       }
       group_sync<GW>(g);
-      int before = 0, total = 0, nb = INT_MAX;
+      int total = 0, nb = INT_MAX;
       for (int w = 0; w < GW; ++w) {
-        const int cw = wcnt[w];
-        if (w < wig) before += cw;
-        total += cw;
+        total += wcnt[w];
         nb = min(nb, wnext[w]);
       }
-      if (NUM) {
-        long long off = obeg + rowcount + before;
-        if (cnt * 4 >= (w1 - w0) * 32) {
-          // dense words: lanes take bits, so each store is contiguous
-          for (int j = w0; j < w1; ++j) {
-            const uint32_t wd = bits[j];
-            if (wd == 0u) continue;
-            if ((wd >> lane) & 1u) {
-              const long long o = off + __popc(wd & lanemask_lt());
-              const int jj = j * 32 + lane;
-              if (o < oend) {
-                c_ci[o] = base + jj;
-                c_v[o] = acc[jj];
-              }
-              acc[jj] = T(0);
-            }
-            off += __popc(wd);
-          }
-          __syncwarp();
-          for (int j = w0 + lane; j < w1; j += 32) bits[j] = 0u;
-        } else {
-          // sparse words: lanes take words and walk their set bits
-          for (int jb = w0; jb < w1; jb += 32) {
-            const int j = jb + lane;
-            uint32_t wd = j < w1 ? bits[j] : 0u;
-            const int c = __popc(wd);
-            const int inc = warp_incl_scan(c);
-            long long o = off + inc - c;
-            while (wd) {
-              const int b = __ffs(wd) - 1;
-              wd &= wd - 1;
-              const int jj = j * 32 + b;
-              if (o < oend) {
-                c_ci[o] = base + jj;
-                c_v[o] = acc[jj];
-              }
-              acc[jj] = T(0);
-              ++o;
-            }
-            if (j < w1) bits[j] = 0u;
-            off += __shfl_sync(FULL, inc, 31);
+      if (split) {
+        const int ntw = min(NTW, sp.ntf - tile0);
+        for (int t = wig * 32 + lane; t < ntw; t += GW * 32) {
+          const int v = tcnt[t];
+          if (v) {
+            atomicAdd(&sp.hcnt[(size_t)idx * sp.ntf + tile0 + t], v);
+            tcnt[t] = 0;
           }
         }
       }
@@ -350,12 +385,9 @@ k_window(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowIn
       group_sync<GW>(g);
       first = false;
       if (nb == INT_MAX) break;
-      base = nb;
+      base = nb & ~31;
     }
-    if (wig == 0 && lane == 0) {
-      if (!NUM) c_cnt[r] = (int)rowcount;
-      else if (obeg + rowcount != oend) atomicOr(err, EB_INTERNAL);
-    }
+    if (wig == 0 && lane == 0) c_cnt[r] = (int)rowcount;
   }
 }
 

@@ -12,66 +12,79 @@ constexpr int SYM_BLOCK_WARPS = 16;
 
 static long long rows_in(const int* path_rows, int p) { return path_rows ? path_rows[p] : -1; }
 
-cudaError_t launch_symbolic(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
-                            const PathBins& pb, const Tuning& tu, int32_t* cursor, int32_t* c_cnt,
-                            const int* path_rows) {
-  (void)tu;
+template <int G, int E>
+static cudaError_t tiny_sym(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri, int lo, int hi,
+                            int32_t* c_cnt, long long rows) {
   const double* nv = nullptr;
   double* nvo = nullptr;
-  // register-sort path: bins 1..4 -> 8 lanes, 5 -> 16 lanes, 6 -> 32 lanes
+  auto k = k_tiny<G, E, false, double>;
+  const int occ = kernel_blocks_per_sm(k, 256, 0);
+  const int grid = persistent_grid(rows, 8 * (32 / G), c.nsm, occ);
+  k<<<grid, 256, 0, c.stream>>>(A, B, nv, nv, ri, c.st, lo, hi, c_cnt, nullptr, nullptr, nvo, c.err);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+// Register-sort bins: 1..4 -> 8 lanes, 5 -> 16 lanes, 6 -> 32 lanes,
+// 7 -> 32 lanes x 2 slots, 8 -> 32 lanes x 4 slots (P <= 128).
+template <typename F8, typename F16, typename F32, typename F64, typename F128>
+static cudaError_t tiny_dispatch(int lo, int hi, F8 f8, F16 f16, F32 f32, F64 f64, F128 f128) {
+  cudaError_t e = cudaSuccess;
+  auto clip = [&](int a, int b, auto f) -> cudaError_t {
+    const int l = lo > a ? lo : a, h = hi < b ? hi : b;
+    return l <= h ? f(l, h) : cudaSuccess;
+  };
+  if ((e = clip(1, 4, f8))) return e;
+  if ((e = clip(5, 5, f16))) return e;
+  if ((e = clip(6, 6, f32))) return e;
+  if ((e = clip(7, 7, f64))) return e;
+  if ((e = clip(8, 8, f128))) return e;
+  return cudaSuccess;
+}
+
+template <int GW, int CW, int W>
+static cudaError_t window_sym(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri, int lo, int hi,
+                              const SplitInfo& sp, int32_t* cursor, int32_t* c_cnt, long long rows) {
+  auto k = k_sym_window<GW, CW, W>;
+  const size_t smem = (size_t)(CW / GW) * sym_group_bytes<W, GW>();
+  const int occ = kernel_blocks_per_sm(k, CW * 32, smem);
+  if (occ <= 0) return cudaErrorInvalidConfiguration;
+  const int grid = persistent_grid(rows, CW / GW, c.nsm, occ);
+  k<<<grid, CW * 32, smem, c.stream>>>(A, B, ri, c.st, lo, hi, sp, cursor, c_cnt, c.err);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symbolic(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
+                            const PathBins& pb, const Tuning& tu, const SplitInfo& sp, int32_t* cursor,
+                            int32_t* c_cnt, const int* path_rows) {
+  (void)tu;
+  cudaError_t e = cudaSuccess;
   if (pb.hi[PATH_TINY] >= pb.lo[PATH_TINY]) {
     timer_mark(c, T_SYM_TINY, 0);
-    const int lo = pb.lo[PATH_TINY], hi = pb.hi[PATH_TINY];
-    const int ranges[3][2] = {{lo, hi < 4 ? hi : 4}, {5 > lo ? 5 : lo, hi < 5 ? hi : 5}, {6 > lo ? 6 : lo, hi}};
-    for (int t = 0; t < 3; ++t) {
-      if (ranges[t][1] < ranges[t][0]) continue;
-      const int G = 8 << t;
-      int occ = 0;
-      int grid;
-      if (G == 8) {
-        occ = kernel_blocks_per_sm(k_tiny<8, false, double>, 256, 0);
-        grid = persistent_grid(rows_in(path_rows, PATH_TINY), 8 * 4, c.nsm, occ);
-        k_tiny<8, false, double><<<grid, 256, 0, c.stream>>>(A, B, nv, nv, ri, c.st, ranges[t][0], ranges[t][1], c_cnt, nullptr, nullptr, nvo, c.err);
-      } else if (G == 16) {
-        occ = kernel_blocks_per_sm(k_tiny<16, false, double>, 256, 0);
-        grid = persistent_grid(rows_in(path_rows, PATH_TINY), 8 * 2, c.nsm, occ);
-        k_tiny<16, false, double><<<grid, 256, 0, c.stream>>>(A, B, nv, nv, ri, c.st, ranges[t][0], ranges[t][1], c_cnt, nullptr, nullptr, nvo, c.err);
-      } else {
-        occ = kernel_blocks_per_sm(k_tiny<32, false, double>, 256, 0);
-        grid = persistent_grid(rows_in(path_rows, PATH_TINY), 8, c.nsm, occ);
-        k_tiny<32, false, double><<<grid, 256, 0, c.stream>>>(A, B, nv, nv, ri, c.st, ranges[t][0], ranges[t][1], c_cnt, nullptr, nullptr, nvo, c.err);
-      }
-      count_launch(c);
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-    }
+    const long long rows = rows_in(path_rows, PATH_TINY);
+    e = tiny_dispatch(pb.lo[PATH_TINY], pb.hi[PATH_TINY],
+        [&](int l, int h) { return tiny_sym<8, 1>(c, A, B, ri, l, h, c_cnt, rows); },
+        [&](int l, int h) { return tiny_sym<16, 1>(c, A, B, ri, l, h, c_cnt, rows); },
+        [&](int l, int h) { return tiny_sym<32, 1>(c, A, B, ri, l, h, c_cnt, rows); },
+        [&](int l, int h) { return tiny_sym<32, 2>(c, A, B, ri, l, h, c_cnt, rows); },
+        [&](int l, int h) { return tiny_sym<32, 4>(c, A, B, ri, l, h, c_cnt, rows); });
     timer_mark(c, T_SYM_TINY, 1);
+    if (e) return e;
   }
   if (pb.hi[PATH_WARP] >= pb.lo[PATH_WARP]) {
     timer_mark(c, T_SYM_WARP, 0);
-    auto k = k_window<1, 8, SYM_WARP_W, false, double>;
-    const size_t smem = 8 * window_group_bytes<SYM_WARP_W, false, double>(1);
-    const int occ = kernel_blocks_per_sm(k, 256, smem);
-    if (occ <= 0) return cudaErrorInvalidConfiguration;
-    const int grid = persistent_grid(rows_in(path_rows, PATH_WARP), 8, c.nsm, occ);
-    k<<<grid, 256, smem, c.stream>>>(A, B, nv, nv, ri, c.st, pb.lo[PATH_WARP], pb.hi[PATH_WARP], cursor, c_cnt, nullptr, nullptr, nvo, c.err);
-    count_launch(c);
+    e = window_sym<1, 8, SYM_WARP_W>(c, A, B, ri, pb.lo[PATH_WARP], pb.hi[PATH_WARP], sp, cursor, c_cnt,
+                                      rows_in(path_rows, PATH_WARP));
     timer_mark(c, T_SYM_WARP, 1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e) return e;
   }
   if (pb.hi[PATH_BLOCK] >= pb.lo[PATH_BLOCK]) {
     timer_mark(c, T_SYM_BLOCK, 0);
-    auto k = k_window<SYM_BLOCK_WARPS, SYM_BLOCK_WARPS, SYM_BLOCK_W, false, double>;
-    const size_t smem = window_group_bytes<SYM_BLOCK_W, false, double>(SYM_BLOCK_WARPS);
-    const int occ = kernel_blocks_per_sm(k, SYM_BLOCK_WARPS * 32, smem);
-    if (occ <= 0) return cudaErrorInvalidConfiguration;
-    const int grid = persistent_grid(rows_in(path_rows, PATH_BLOCK), 1, c.nsm, occ);
-    k<<<grid, SYM_BLOCK_WARPS * 32, smem, c.stream>>>(A, B, nv, nv, ri, c.st, pb.lo[PATH_BLOCK], pb.hi[PATH_BLOCK], cursor, c_cnt, nullptr, nullptr, nvo, c.err);
-    count_launch(c);
+    e = window_sym<SYM_BLOCK_WARPS, SYM_BLOCK_WARPS, SYM_BLOCK_W>(c, A, B, ri, pb.lo[PATH_BLOCK], pb.hi[PATH_BLOCK],
+                                                                 sp, cursor, c_cnt, rows_in(path_rows, PATH_BLOCK));
     timer_mark(c, T_SYM_BLOCK, 1);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    if (e) return e;
   }
   return cudaSuccess;
 }

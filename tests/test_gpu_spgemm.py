@@ -220,3 +220,56 @@ def test_rmat_scale14(api, oracle_mod):
     assert_structure_equal(C, R)
     assert_values_close(C.vals, R.vals, S)
     assert stats[0] == int(oracle_mod.row_products(A, A).sum())
+
+
+@pytest.mark.parametrize("split_min", [64, 2000, 50000])
+@pytest.mark.parametrize("window", [1024, 2048, 4096])
+def test_split_rows_and_windows(api, oracle_mod, split_min, window):
+    """Heavy rows split into column tiles (per-tile counts from the symbolic
+    pass, tile bounds from the B-row tile table), for each window width."""
+    rng = np.random.default_rng(11)
+    counts = rng.integers(0, 300, size=96)
+    counts[:4] = [2500, 1200, 700, 400]
+    A = gen.random_rows(96, 5000, counts, rng)
+    cB = rng.integers(0, 40, size=5000)
+    cB[:30] = 9000
+    B = gen.random_rows(5000, 40000, cB, rng)
+    C, _ = run(api, A, B, split_min=split_min, window_warp=window)
+    R, S = oracle_with_scale(oracle_mod, A, B)
+    assert_structure_equal(C, R)
+    assert_values_close(C.vals, R.vals, S)
+
+
+@pytest.mark.parametrize("split_min", [128, 4096])
+def test_rmat_scale12_split_integer(api, oracle_mod, split_min):
+    A = gen.rmat(12, 16)
+    A.vals = np.round(A.vals * 4)  # integer values: bit-exact
+    C, _ = run(api, A, A, split_min=split_min)
+    R = oracle_mod.spgemm(A, A)
+    assert_structure_equal(C, R)
+    assert_values_exact(C.vals, R.vals)
+
+
+def test_many_nonzeros_per_row_global_cursors(api, oracle_mod):
+    """Rows with more than 256 nonzeros keep their cursors in global memory."""
+    rng = np.random.default_rng(5)
+    counts = rng.integers(200, 900, size=40)
+    A = gen.random_rows(40, 3000, counts, rng)
+    B = gen.random_rows(3000, 9000, rng.integers(0, 12, size=3000), rng)
+    C, _ = run(api, A, B, split_min=-1)
+    R, S = oracle_with_scale(oracle_mod, A, B)
+    assert_structure_equal(C, R)
+    assert_values_close(C.vals, R.vals, S)
+
+
+@pytest.mark.parametrize("P", [65, 96, 127, 128, 129])
+def test_register_sort_multi_slot(api, oracle_mod, P):
+    rng = np.random.default_rng(P)
+    B = gen.random_rows(P, 200, np.ones(P, np.int64), rng, values="int")
+    A = gen.CSR(2, P, np.array([0, P, 2 * P], np.int32),
+                np.concatenate([np.arange(P), np.arange(P)]).astype(np.int32),
+                np.ones(2 * P))
+    C, _ = run(api, A, B)
+    R = oracle_mod.spgemm(A, B)
+    assert_structure_equal(C, R)
+    assert_values_exact(C.vals, R.vals)
