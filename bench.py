@@ -279,7 +279,12 @@ def kernel_bytes(A, B, prod_rows, c_rp, kernel, row_begin):
     kernel's rows."""
     P = np.asarray(prod_rows, np.int64)
     path = kernel.split("_", 1)[1]
-    lo, hi = {"tiny": (1, 32), "warp": (33, 8192), "block": (8193, 1 << 62), "hash": (0, -1)}[path]
+    # register sort up to 128 products; every larger row runs in the warp
+    # window kernel (numeric) / the bitmap kernels (symbolic warp <= 8192 < block)
+    if kernel.startswith("num"):
+        lo, hi = {"tiny": (1, 128), "warp": (129, 1 << 62)}.get(path, (0, -1))
+    else:
+        lo, hi = {"tiny": (1, 128), "warp": (129, 8192), "block": (8193, 1 << 62)}.get(path, (0, -1))
     rows = np.flatnonzero((P >= lo) & (P <= hi))
     if len(rows) == 0:
         return 0.0

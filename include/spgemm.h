@@ -83,7 +83,7 @@ typedef struct spgemm_opts {
   int32_t hash_max;    /* rows of at most this many products use the shared-memory
                           hash accumulator (0: library default; -1: never) */
   int32_t window_warp; /* columns of the numeric dense window (one per warp):
-                          1024, 2048 or 4096 (0: default 2048) */
+                          1024, 2048 or 4096 (0: default 1024) */
   int32_t window_block;/* reserved, keep 0 */
   int32_t split_min;   /* rows with more products than this are split into column
                           tiles of window_warp columns, processed independently

@@ -126,40 +126,64 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const long long* __restrict
 
 static int grid_for_warps(long long nwarps, int warps_per_block, int nsm);
 
-// First index of each coarse column tile in each row of B (one warp per
-// row): bnd[k][t] = first position of row k whose column is >= t * Tc, and
-// bnd[k][ntc] = end of the row.  Lets a split row find the part of B(k,:)
-// inside a tile without scanning from the row start.  Skipped when no row
-// is split.
-__global__ void __launch_bounds__(256) k_tile_bounds(Csr B, SplitInfo sp, const DevStats* st) {
-  __shared__ int s_any;
-  if (threadIdx.x == 0) s_any = split_rows(st, sp) > 0;
-  if (block_skip(st) || !s_any) return;
+// Window-run list of B (see SplitInfo): pass 1 counts the runs of each row
+// (plus its sentinel), an exclusive scan turns counts into run pointers,
+// pass 2 writes (window id, first position) of every run.  One warp per row;
+// a run starts where the window id differs from the previous entry's.
+__global__ void __launch_bounds__(256) k_runs_count(Csr B, int wshift, int32_t* __restrict__ rr, const DevStats* st) {
+  if (block_skip(st)) return;
   const int lane = lane_id();
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
-  const int stride = sp.ntc + 1;
   for (long long k = w; k < B.nrows; k += nw) {
-    int32_t* bk = sp.bnd + k * stride;
     const int rs = B.rp[k], re = B.rp[k + 1];
-    if (rs == re) {
-      for (int t = lane; t < stride; t += 32) bk[t] = rs;
-      continue;
-    }
-    if (lane == 0) bk[0] = rs;
+    int n = 0;
     for (int idx = rs + lane; idx < re; idx += 32) {
-      const int tcur = B.ci[idx] >> sp.tc_shift;
-      const int tprev = idx > rs ? (B.ci[idx - 1] >> sp.tc_shift) : 0;
-      for (int t = tprev + 1; t <= tcur && t <= sp.ntc; ++t) bk[t] = idx;
-      if (idx == re - 1)
-        for (int t = tcur + 1; t <= sp.ntc; ++t) bk[t] = re;
+      const int wid = B.ci[idx] >> wshift;
+      const bool start = idx == rs || (B.ci[idx - 1] >> wshift) != wid;
+      n += __popc(__ballot_sync(__activemask(), start));
     }
+    n = __shfl_sync(FULL, n, 0);
+    if (lane == 0) rr[k] = n + 1;
   }
 }
 
-cudaError_t launch_tile_bounds(const LaunchCtx& c, const Csr& B, const SplitInfo& sp) {
-  if (sp.heavy_bin >= NBINS || B.nrows <= 0 || !sp.bnd) return cudaSuccess;
-  k_tile_bounds<<<grid_for_warps(B.nrows, 8, c.nsm), 256, 0, c.stream>>>(B, sp, c.st);
+__global__ void __launch_bounds__(256) k_runs_fill(Csr B, int wshift, const int32_t* __restrict__ rr,
+                                                   int2* __restrict__ runs, const DevStats* st) {
+  if (block_skip(st)) return;
+  const int lane = lane_id();
+  const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
+  for (long long k = w; k < B.nrows; k += nw) {
+    const int rs = B.rp[k], re = B.rp[k + 1];
+    int pos = rr[k];
+    for (int base = rs; base < re; base += 32) {
+      const int idx = base + lane;
+      bool start = false;
+      int wid = 0;
+      if (idx < re) {
+        wid = B.ci[idx] >> wshift;
+        start = idx == rs || (B.ci[idx - 1] >> wshift) != wid;
+      }
+      const unsigned m = __ballot_sync(FULL, start);
+      if (start) runs[pos + __popc(m & lanemask_lt())] = make_int2(wid, idx);
+      pos += __popc(m);
+    }
+    if (lane == 0) runs[rr[k + 1] - 1] = make_int2(INT_MAX, re);
+  }
+}
+
+cudaError_t launch_runs(const LaunchCtx& c, const Csr& B, const SplitInfo& sp, long long* partials) {
+  if (!sp.rr || !sp.runs) return cudaSuccess;
+  if (B.nrows <= 0) return cudaMemsetAsync(sp.rr, 0, sizeof(int32_t), c.stream);
+  const int grid = grid_for_warps(B.nrows, 8, c.nsm);
+  k_runs_count<<<grid, 256, 0, c.stream>>>(B, sp.wf_shift, sp.rr, c.st);
+  count_launch(c);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_scan(c, sp.rr, B.nrows, partials, &c.st->nruns);
+  if (e != cudaSuccess) return e;
+  k_runs_fill<<<grid, 256, 0, c.stream>>>(B, sp.wf_shift, sp.rr, sp.runs, c.st);
   count_launch(c);
   return cudaGetLastError();
 }

@@ -23,6 +23,7 @@ struct spgemm_plan {
   int32_t* cursor = nullptr;
   int32_t* nxt = nullptr;
   long long* scan_part = nullptr;
+  long long* runs_part = nullptr;
   // host state
   sg::PathBins pb{};
   sg::Tuning tu{};
@@ -49,50 +50,43 @@ constexpr size_t ALIGN = 256;
 inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 
 struct Layout {
-  size_t st, prod, cmin, cmax, rows, cursor, nxt, scan, bnd, hcnt, total;
+  size_t st, prod, cmin, cmax, rows, cursor, nxt, scan, rr, runs, runs_part, hcnt, total;
 };
 
-// Split geometry from the options and B's width (see sg::SplitInfo).
-void split_geometry(const spgemm_opts& o, int window, long long mloc, long long nrows_b, long long ncols_b,
-                    sg::SplitInfo* sp, size_t* bnd_entries, size_t* hcnt_entries) {
+// Window geometry and split capacity from the options and B's width (see
+// sg::SplitInfo).  *hcnt_entries is 0 when no row is split.
+void split_geometry(const spgemm_opts& o, int window, long long mloc, long long ncols_b, sg::SplitInfo* sp,
+                    size_t* hcnt_entries) {
   sp->heavy_bin = sg::NBINS;
   sp->hcap = 0;
   sp->wf_shift = 0;
   while ((1 << sp->wf_shift) < window) ++sp->wf_shift;
   sp->ntf = (int)((ncols_b + window - 1) / window);
-  long long tc = 8ll * window;
-  while ((ncols_b + tc - 1) / tc > 64) tc <<= 1;
-  sp->tc_shift = 0;
-  while ((1ll << sp->tc_shift) < tc) ++sp->tc_shift;
-  sp->ntc = (int)((ncols_b + tc - 1) / tc);
-  *bnd_entries = 0;
   *hcnt_entries = 0;
   if (o.split_min < 0 || o.force_path >= 0 || mloc <= 0 || sp->ntf < 2) return;
   const long long smin = o.split_min > 0 ? o.split_min : 131072;
-  const size_t bnd = (size_t)nrows_b * (size_t)(sp->ntc + 1);
-  if (bnd > (size_t)1 << 28) return;  // table would be too large: never split
   long long cap = mloc < 16384 ? mloc : 16384;
   const long long lim = ((long long)1 << 24) / sp->ntf;
   if (cap > lim) cap = lim;
   if (cap <= 0) return;
   // split rows always lie above the register-sort bins (1..8), so their
-  // sizes come from the bitmap-window kernel, which records per-tile counts
+  // sizes come from the bitmap-window kernel, which records per-window counts
   sp->heavy_bin = sg::bin_of(smin) + 1;
   if (sp->heavy_bin < 9) sp->heavy_bin = 9;
   if (sp->heavy_bin >= sg::NBINS) { sp->heavy_bin = sg::NBINS; return; }
   sp->hcap = (int)cap;
-  *bnd_entries = bnd;
   *hcnt_entries = (size_t)cap * (size_t)sp->ntf;
 }
 
 int numeric_window(const spgemm_opts& o) {
-  return (o.window_warp == 1024 || o.window_warp == 4096) ? o.window_warp : 2048;
+  return (o.window_warp == 2048 || o.window_warp == 4096) ? o.window_warp : 1024;
 }
 
-Layout layout_for(const spgemm_opts& o, long long mloc, long long nnz_a, long long nrows_b, long long ncols_b) {
+Layout layout_for(const spgemm_opts& o, long long mloc, long long nnz_a, long long nrows_b, long long ncols_b,
+                  long long nnz_b) {
   sg::SplitInfo sp;
-  size_t nb = 0, nh = 0;
-  split_geometry(o, numeric_window(o), mloc, nrows_b, ncols_b, &sp, &nb, &nh);
+  size_t nh = 0;
+  split_geometry(o, numeric_window(o), mloc, ncols_b, &sp, &nh);
   Layout L{};
   size_t off = 0;
   L.st = off; off = align_up(off + sizeof(sg::DevStats));
@@ -103,7 +97,9 @@ Layout layout_for(const spgemm_opts& o, long long mloc, long long nnz_a, long lo
   L.cursor = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
   L.nxt = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
   L.scan = off; off = align_up(off + sizeof(long long) * sg::scan_partials_count(mloc));
-  L.bnd = off; off = align_up(off + sizeof(int32_t) * nb);
+  L.rr = off; off = align_up(off + sizeof(int32_t) * (size_t)(nrows_b + 1));
+  L.runs = off; off = align_up(off + sizeof(int2) * (size_t)(nnz_b + nrows_b));
+  L.runs_part = off; off = align_up(off + sizeof(long long) * sg::scan_partials_count(nrows_b));
   L.hcnt = off; off = align_up(off + sizeof(int32_t) * nh);
   L.total = off;
   return L;
@@ -244,7 +240,7 @@ spgemm_status spgemm_workspace_size(const spgemm_csr* A, const spgemm_csr* B, co
   if (opts) o = *opts; else spgemm_opts_default(&o);
   const long long rb = o.row_begin, re = o.row_end < 0 ? A->nrows : o.row_end;
   if (rb < 0 || re < rb || re > A->nrows) return SPGEMM_ERR_DIM_MISMATCH;
-  *bytes = layout_for(o, re - rb, A->nnz, B->nrows, B->ncols).total;
+  *bytes = layout_for(o, re - rb, A->nnz, B->nrows, B->ncols, B->nnz).total;
   return SPGEMM_OK;
 }
 
@@ -263,7 +259,7 @@ spgemm_status spgemm_analyse(const spgemm_csr* A, const spgemm_csr* B, const spg
   if (o.force_path < -1 || o.force_path > 4) return SPGEMM_ERR_INVALID_ARG;
   const long long rb = o.row_begin, re = o.row_end < 0 ? A->nrows : o.row_end;
   if (rb < 0 || re < rb || re > A->nrows) return SPGEMM_ERR_DIM_MISMATCH;
-  const Layout L = layout_for(o, re - rb, A->nnz, B->nrows, B->ncols);
+  const Layout L = layout_for(o, re - rb, A->nnz, B->nrows, B->ncols, B->nnz);
   if (!workspace || workspace_bytes < L.total) return SPGEMM_ERR_WORKSPACE;
   if (((uintptr_t)workspace) % 16) return SPGEMM_ERR_WORKSPACE;
 
@@ -289,10 +285,12 @@ spgemm_status spgemm_analyse(const spgemm_csr* A, const spgemm_csr* B, const spg
   p->scan_part = (long long*)(p->ws + L.scan);
   choose_paths(o, &p->pb, &p->tu);
   {
-    size_t nb = 0, nh = 0;
-    split_geometry(o, p->tu.window_warp, p->mloc, B->nrows, B->ncols, &p->sp, &nb, &nh);
-    p->sp.bnd = nb ? (int32_t*)(p->ws + L.bnd) : nullptr;
+    size_t nh = 0;
+    split_geometry(o, p->tu.window_warp, p->mloc, B->ncols, &p->sp, &nh);
+    p->sp.rr = (int32_t*)(p->ws + L.rr);
+    p->sp.runs = (int2*)(p->ws + L.runs);
     p->sp.hcnt = nh ? (int32_t*)(p->ws + L.hcnt) : nullptr;
+    p->runs_part = (long long*)(p->ws + L.runs_part);
   }
 
   cudaStream_t st = (cudaStream_t)stream;
@@ -303,7 +301,7 @@ spgemm_status spgemm_analyse(const spgemm_csr* A, const spgemm_csr* B, const spg
     if (e == cudaSuccess) e = sg::launch_validate(c, p->B);
   }
   if (e == cudaSuccess) e = sg::launch_analyse(c, p->A, p->B, p->row_begin, p->mloc, p->prod, p->cmin, p->cmax, p->rows);
-  if (e == cudaSuccess) e = sg::launch_tile_bounds(c, p->B, p->sp);
+  if (e == cudaSuccess) e = sg::launch_runs(c, p->B, p->sp, p->runs_part);
   if (e != cudaSuccess) { delete p; return SPGEMM_ERR_CUDA; }
   *plan = p;
   return SPGEMM_OK;

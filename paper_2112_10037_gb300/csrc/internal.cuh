@@ -7,7 +7,7 @@
 #include <cstddef>
 #include <cstdint>
 
-#include "../../include/spgemm.h"
+#include "spgemm.h"  // include/ is on the include path (see build.py)
 
 namespace sg {
 
@@ -42,6 +42,7 @@ struct DevStats {
   unsigned long long total_products;
   unsigned long long max_products;
   long long nnz_c;
+  long long nruns;   // entries of B's window-run list
   uint32_t err;
   uint32_t pad;
   int hist[NBINS];   // rows per bin
@@ -84,18 +85,23 @@ struct Tuning {
   int warp_max;        // largest P of the symbolic warp path
 };
 
-// Splitting of heavy rows into column tiles (numeric pass) and the tables
-// the split needs.  Heavy rows are the leading rows of the descending-bin
-// list whose bin is >= heavy_bin, at most hcap of them; row h of the list
-// owns hcnt[h * ntf .. h * ntf + ntf).
+// Window-run list of B: the numeric pass uses windows of 2^wf_shift columns
+// aligned to multiples of their width.  Each row k of B is cut into runs of
+// consecutive entries that fall in the same window; run j of the list holds
+// (window id, first position in B), rows own runs [rr[k], rr[k+1]), and the
+// last run of each row is a sentinel (INT_MAX, end of row) so run j covers
+// positions [start_j, start_{j+1}).
+//
+// Splitting of heavy rows into window tiles (numeric pass): heavy rows are
+// the leading rows of the descending-bin list whose bin is >= heavy_bin, at
+// most hcap of them; row h of the list owns hcnt[h * ntf .. h * ntf + ntf).
 struct SplitInfo {
   int heavy_bin;      // NBINS disables splitting
   int hcap;
-  int wf_shift;       // log2 of the fine tile width (= numeric window)
-  int ntf;            // fine tiles per row: ceil(ncols(B) / fine width)
-  int tc_shift;       // log2 of the coarse tile width
-  int ntc;            // coarse tiles per row: ceil(ncols(B) / coarse width)
-  int32_t* bnd;       // nrows(B) x (ntc + 1): first index of each coarse tile in each B row
+  int wf_shift;       // log2 of the window (= fine tile) width
+  int ntf;            // windows per row: ceil(ncols(B) / width)
+  int32_t* rr;        // nrows(B) + 1 run pointers
+  int2* runs;         // (window id, start) per run, sentinel-terminated rows
   int32_t* hcnt;      // hcap x ntf output counts
 };
 
@@ -205,11 +211,12 @@ inline void count_launch(const LaunchCtx& c) {
 cudaError_t launch_validate(const LaunchCtx& c, const Csr& M);
 cudaError_t launch_analyse(const LaunchCtx& c, const Csr& A, const Csr& B, long long row_begin,
                            long long mloc, long long* prod, int* cmin, int* cmax, int* rows);
-cudaError_t launch_tile_bounds(const LaunchCtx& c, const Csr& B, const SplitInfo& sp);
+cudaError_t launch_runs(const LaunchCtx& c, const Csr& B, const SplitInfo& sp, long long* partials);
 cudaError_t launch_symbolic(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
                             const PathBins& pb, const Tuning& tu, const SplitInfo& sp, int32_t* cursor,
                             int32_t* c_rp, const int* path_rows /* host, may be null */);
-cudaError_t launch_scan(const LaunchCtx& c, int32_t* c_rp, long long mloc, long long* partials);
+cudaError_t launch_scan(const LaunchCtx& c, int32_t* c_rp, long long mloc, long long* partials,
+                        long long* total_out = nullptr);
 size_t scan_partials_count(long long mloc);
 cudaError_t launch_numeric(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
                            const PathBins& pb, const Tuning& tu, const SplitInfo& sp, int dtype,

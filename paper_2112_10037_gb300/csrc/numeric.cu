@@ -28,16 +28,15 @@ static cudaError_t warp_num(const LaunchCtx& c, const Csr& A, const Csr& B, cons
                             const RowInfo& ri, int lo, int hi, const SplitInfo& sp, int32_t* cur, int32_t* nxt,
                             const int32_t* c_rp, int32_t* c_ci, T* c_v) {
   auto k = k_num_warp<W, NUM_WARPS_CTA, T>;
-  const size_t smem = (size_t)NUM_WARPS_CTA * ((size_t)W * sizeof(T) + W);
+  const size_t smem = (size_t)NUM_WARPS_CTA * ((size_t)W * sizeof(T) + W / 8);
   const int occ = kernel_blocks_per_sm(k, NUM_WARPS_CTA * 32, smem);
   if (occ <= 0) return cudaErrorInvalidConfiguration;
   NumSplit ns;
   ns.heavy_bin = sp.heavy_bin;
   ns.hcap = sp.hcap;
   ns.ntf = sp.ntf;
-  ns.ntc = sp.ntc;
-  ns.tc_shift = sp.tc_shift;
-  ns.bnd = sp.bnd;
+  ns.rr = sp.rr;
+  ns.runs = sp.runs;
   ns.hcnt = sp.hcnt;
   ns.counter = &c.st->work[0];
   cudaError_t e = cudaMemsetAsync(ns.counter, 0, sizeof(unsigned), c.stream);
@@ -93,9 +92,9 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
   if (hi >= lo) {
     timer_mark(c, T_NUM_WARP, 0);
     switch (tu.window_warp) {
-      case 1024: e = warp_num<T, 1024>(c, A, B, av, bv, ri, lo, hi, sp, cur, nxt, c_rp, c_ci, c_v); break;
+      case 2048: e = warp_num<T, 2048>(c, A, B, av, bv, ri, lo, hi, sp, cur, nxt, c_rp, c_ci, c_v); break;
       case 4096: e = warp_num<T, 4096>(c, A, B, av, bv, ri, lo, hi, sp, cur, nxt, c_rp, c_ci, c_v); break;
-      default: e = warp_num<T, 2048>(c, A, B, av, bv, ri, lo, hi, sp, cur, nxt, c_rp, c_ci, c_v); break;
+      default: e = warp_num<T, 1024>(c, A, B, av, bv, ri, lo, hi, sp, cur, nxt, c_rp, c_ci, c_v); break;
     }
     timer_mark(c, T_NUM_WARP, 1);
     if (e) return e;

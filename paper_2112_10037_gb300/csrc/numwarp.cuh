@@ -2,27 +2,29 @@
 //
 // Row i of C is the sum over A(i,k) of A(i,k) * B(k,:) (Sec. 2.2).  A warp
 // owns a window of W consecutive columns in shared memory: a dense value
-// array and an "owner" byte per column (nonzero = the column is present).
+// array and a presence bit per column.
 // Rows of B are sorted, so the part of B(k,:) inside a window is one
-// contiguous segment, found from a per-nonzero cursor.  Each product is
-// accumulated with one fused multiply-add, acc[j] = fma(A(i,k), B(k,j), acc[j]),
-// with no atomics: only this warp touches the window, lanes that walk one
-// segment hit distinct columns, and when lanes carry products of different
-// segments a lane first claims its column by writing its id into the owner
-// byte; the lanes that read their own id back update, the rest retry.  The
-// window is emitted in column order by a popcount prefix over the owner
-// bytes, so no sort is needed, and cleared on the way out.
+// contiguous segment.  Only this warp touches the window.  When the warp
+// walks one long segment its lanes hit distinct columns, so each product is
+// one fused multiply-add, acc[j] = fma(A(i,k), B(k,j), acc[j]), without
+// atomics.  Products of several short segments are spread over the lanes
+// and may share columns; those go through shared-memory atomic adds.  The
+// window is emitted in column order by a popcount prefix over a presence
+// bitmap, so no sort is needed, and cleared on the way out.
+//
+// Windows are aligned to multiples of W, and B comes with its window-run
+// list (runs of entries of one row inside one window, see SplitInfo), so the
+// segment of B(k,:) in a window is exactly one run: [start_j, start_{j+1}).
 //
 // Work items, handed out largest first through a global counter:
 //  * split rows (heavy rows, product count above a threshold): one item per
-//    tile of W columns aligned to multiples of W.  The item finds each
-//    nonzero's segment by binary search inside a coarse tile of the B-row
-//    tile-boundary table, and writes at the offset given by the per-tile
-//    output counts of the symbolic pass.
-//  * other rows: one item per row, swept window by window from its smallest
-//    column; the next window starts at the smallest unread column.  Cursors
-//    live in registers (up to 32 * SLOTS nonzeros per row) or in global
-//    arrays parallel to A's nonzeros.
+//    window of the row.  Each nonzero finds its run for the window by binary
+//    search over the runs of its B row; the item writes at the offset given
+//    by the per-window output counts of the symbolic pass.
+//  * other rows: one item per row, swept window by window; the next window
+//    is the smallest window id among the nonzeros' current runs.  Each
+//    nonzero's run cursor lives in registers (up to 32 * SLOTS nonzeros per
+//    row) or in global arrays parallel to A's nonzeros.
 #pragma once
 
 #include "internal.cuh"
@@ -31,36 +33,29 @@ namespace sg {
 
 struct NumSplit {
   int heavy_bin;          // rows in bins >= heavy_bin are split (within capacity)
-  int hcap;               // capacity of the per-tile count table (rows)
-  int ntf;                // fine tiles (of W columns) per row
-  int ntc;                // coarse tiles per row
-  int tc_shift;           // log2 of the coarse tile width
-  const int32_t* bnd;     // B-row coarse tile boundaries, nrows(B) x (ntc + 1)
-  const int32_t* hcnt;    // output counts per (split row, fine tile)
+  int hcap;               // capacity of the per-window count table (rows)
+  int ntf;                // windows (of W columns) per row
+  const int32_t* rr;      // B's run pointers (nrows(B) + 1)
+  const int2* runs;       // B's runs: (window id, start), sentinel per row
+  const int32_t* hcnt;    // output counts per (split row, window)
   unsigned* counter;      // work counter, zero before the launch
 };
 
 constexpr int NW_SLOTS = 8;  // register cursors: up to 256 nonzeros of A per row
 
-__device__ __forceinline__ unsigned byte_mask16(const uint4 q) {
-  auto m4 = [](unsigned w) -> unsigned {
-    const unsigned nz = __vcmpne4(w, 0u) & 0x01010101u;
-    return (nz * 0x01020408u) >> 24;
-  };
-  return m4(q.x) | (m4(q.y) << 4) | (m4(q.z) << 8) | (m4(q.w) << 12);
-}
-
 template <int W, typename T>
 struct WarpWin {
   T* acc;
-  uint8_t* own;
+  uint32_t* bits;   // presence bitmap, W / 32 words
   uint32_t* err;
+
+  __device__ __forceinline__ void mark(int j) { atomicOr(&bits[j >> 5], 1u << (j & 31)); }
 
   // Lanes carry products of one segment: distinct columns, no claim needed.
   __device__ __forceinline__ void add_distinct(int j, T a, T b, bool act) {
     if (act) {
       if ((unsigned)j < (unsigned)W) {
-        own[j] = 1;
+        mark(j);
         acc[j] = fma(a, b, acc[j]);
       } else {
         atomicOr(err, EB_UNSORTED);
@@ -68,23 +63,17 @@ struct WarpWin {
     }
   }
 
-  // Lanes may carry equal columns: claim, check, update, retry.
-  __device__ __forceinline__ void add_claimed(int j, T a, T b, bool act) {
-    const int lane = lane_id();
-    if (act && (unsigned)j >= (unsigned)W) {
-      atomicOr(err, EB_UNSORTED);
-      act = false;
-    }
-    bool pending = act;
-    const uint8_t me = (uint8_t)(lane + 1);
-    while (__any_sync(FULL, pending)) {
-      if (pending) own[j] = me;
-      __syncwarp();
-      if (pending && own[j] == me) {
-        acc[j] = fma(a, b, acc[j]);
-        pending = false;
+  // Lanes may carry equal columns (short segments of different B rows often
+  // share the hub columns): shared-memory atomic add, which resolves equal
+  // addresses in hardware.
+  __device__ __forceinline__ void add_atomic(int j, T a, T b, bool act) {
+    if (act) {
+      if ((unsigned)j < (unsigned)W) {
+        mark(j);
+        atomicAdd(&acc[j], a * b);
+      } else {
+        atomicOr(err, EB_UNSORTED);
       }
-      __syncwarp();
     }
   }
 
@@ -94,6 +83,7 @@ struct WarpWin {
   __device__ __forceinline__ void segments(const Csr& B, const T* __restrict__ bv, int s, int len, T a,
                                            int base) {
     const int lane = lane_id();
+    if (!__any_sync(FULL, len > 0)) return;
     unsigned lm = __ballot_sync(FULL, len >= 32);
     while (lm) {
       const int L = __ffs(lm) - 1;
@@ -135,39 +125,42 @@ struct WarpWin {
         j2 = B.ci[bi] - base;
         b2 = bv[bi];
       }
-      add_claimed(j, oa, b, p < tot);
-      add_claimed(j2, oa2, b2, p2 < tot);
+      add_atomic(j, oa, b, p < tot);
+      add_atomic(j2, oa2, b2, p2 < tot);
     }
+    __syncwarp();
   }
 
-  // Emits the window [base, base + ncols) in column order at out (checked
-  // against out_end), clears it, returns the number of entries.
-  __device__ __forceinline__ long long emit(int base, int ncols, long long out, long long out_end,
-                                            int32_t* __restrict__ c_ci, T* __restrict__ c_v) {
+  // Emits the window [base, base + ncols) in column order at c_ci/c_v + out
+  // (offsets relative to the row's first entry, checked against out_end),
+  // clears it, returns the number of entries.  Lanes take 32-column words;
+  // a warp prefix of their popcounts places each lane's entries.
+  __device__ __forceinline__ int emit(int base, int ncols, int out, int out_end, int32_t* __restrict__ c_ci,
+                                      T* __restrict__ c_v) {
     const int lane = lane_id();
-    const long long start = out;
+    const int start = out;
+    const int nw = (ncols + 31) >> 5;
     __syncwarp();
-    for (int cb = 0; cb < ncols; cb += 512) {
-      uint4* qp = reinterpret_cast<uint4*>(own + cb + lane * 16);
-      const uint4 q = *qp;
-      unsigned m = byte_mask16(q);
+    for (int wb = 0; wb < nw; wb += 32) {
+      const int wi = wb + lane;
+      uint32_t m = wi < nw ? bits[wi] : 0u;
       const int cnt = __popc(m);
       const int inc = warp_incl_scan(cnt);
-      long long pos = out + inc - cnt;
+      int pos = out + inc - cnt;
+      if (m) bits[wi] = 0u;
       while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
-        const int jj = cb + lane * 16 + b;
-        if (pos < out_end) {
-          c_ci[pos] = base + jj;
-          c_v[pos] = acc[jj];
+        const int jj = (wi << 5) + b;
+        if (pos < out_end) {  // C is written once: streaming stores keep B resident in L2
+          __stcs(c_ci + pos, base + jj);
+          __stcs(c_v + pos, acc[jj]);
         } else {
           atomicOr(err, EB_INTERNAL);
         }
         acc[jj] = T(0);
         ++pos;
       }
-      if (cnt) *qp = make_uint4(0u, 0u, 0u, 0u);
       out += __shfl_sync(FULL, inc, 31);
     }
     __syncwarp();
@@ -184,22 +177,33 @@ __device__ __forceinline__ int lower_bound_col(const int32_t* __restrict__ ci, i
   return lo;
 }
 
+// First run of [lo, hi) whose window id is >= w (hi if none).
+__device__ __forceinline__ int lower_bound_run(const int2* __restrict__ runs, int lo, int hi, int w) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (runs[mid].x < w) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 template <int W, int NWARP, typename T>
 __global__ void __launch_bounds__(NWARP * 32)
 k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri, const DevStats* st,
            int bin_lo, int bin_hi, NumSplit sp, int32_t* __restrict__ gcur, int32_t* __restrict__ gnxt,
            const int32_t* __restrict__ c_rp, int32_t* __restrict__ c_ci, T* __restrict__ c_v, uint32_t* err) {
   static_assert(W % 512 == 0, "window must be a multiple of 512 columns");
-  constexpr size_t WB = (size_t)W * sizeof(T) + W;  // per-warp bytes
+  constexpr size_t WB = (size_t)W * sizeof(T) + W / 8;  // per-warp bytes
+  constexpr int WSHIFT = (W == 512) ? 9 : (W == 1024) ? 10 : (W == 2048) ? 11 : (W == 4096) ? 12 : 13;
+  static_assert((1 << WSHIFT) == W, "window must be a power of two");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_lb, s_le, s_nh;
   const int warp = threadIdx.x >> 5, lane = lane_id();
   WarpWin<W, T> win;
   win.acc = reinterpret_cast<T*>(smem_raw + (size_t)warp * WB);
-  win.own = reinterpret_cast<uint8_t*>(smem_raw + (size_t)warp * WB + (size_t)W * sizeof(T));
+  win.bits = reinterpret_cast<uint32_t*>(smem_raw + (size_t)warp * WB + (size_t)W * sizeof(T));
   win.err = err;
   for (int t = lane; t < W; t += 32) win.acc[t] = T(0);
-  for (int t = lane; t < W / 16; t += 32) reinterpret_cast<uint4*>(win.own)[t] = make_uint4(0u, 0u, 0u, 0u);
+  for (int t = lane; t < W / 32; t += 32) win.bits[t] = 0u;
   if (threadIdx.x == 0) {
     int b, e;
     bin_range(st, bin_lo, bin_hi, &b, &e);
@@ -214,7 +218,6 @@ k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
   const int lb = s_lb, le = s_le, nh = s_nh;
   const long long nsplit_items = (long long)nh * sp.ntf;
   const long long total = nsplit_items + (le - lb - nh);
-  const int wshift = 31 - __clz(W);
 
   while (true) {
     long long item = 0;
@@ -222,27 +225,25 @@ k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
     item = __shfl_sync(FULL, item, 0);
     if (item >= total) break;
     if (item < nsplit_items) {
-      // ---- one W-column tile of a split row
-      const int h = (int)(item / sp.ntf), tf = (int)(item % sp.ntf);
+      // ---- one window of a split row
+      const int h = (int)(item / sp.ntf), tw = (int)(item % sp.ntf);
       const int r = ri.rows[lb + h];
       const int cmn = ri.cmin[r], cmx = ri.cmax[r];
-      const int tbase = tf << wshift;
+      const int tbase = tw << WSHIFT;
       if (tbase + W - 1 < cmn || tbase > cmx) continue;
-      // output offset: row start + counts of the row's earlier tiles
       const int32_t* hc = sp.hcnt + (size_t)h * sp.ntf;
       int before = 0;
-      for (int t = lane; t < tf; t += 32) before += hc[t];
+      for (int t = lane; t < tw; t += 32) before += hc[t];
       before = warp_sum(before);
-      const long long out0 = (long long)c_rp[r] + before;
-      const long long out_end = out0 + hc[tf];
-      if (before < 0 || hc[tf] < 0 || out_end > (long long)c_rp[r + 1]) {  // inconsistent counts
+      const long long rbeg = c_rp[r];
+      const int out0 = before;
+      const int out_end = out0 + hc[tw];
+      if (before < 0 || hc[tw] < 0 || rbeg + out_end > (long long)c_rp[r + 1]) {  // inconsistent counts
         if (lane == 0) atomicOr(err, EB_INTERNAL);
         continue;
       }
       const long long i = ri.row_begin + r;
       const int a0 = A.rp[i], a1 = A.rp[i + 1];
-      const int tc = tbase >> sp.tc_shift;
-      const int tend = tbase + W;
       for (int e0 = a0; e0 < a1; e0 += 32) {
         const int e = e0 + lane;
         int s = 0, len = 0;
@@ -250,19 +251,20 @@ k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
         if (e < a1) {
           const int k = A.ci[e];
           a = av[e];
-          const int32_t* bk = sp.bnd + (size_t)k * (sp.ntc + 1) + tc;
-          const int cs = bk[0], ce = bk[1];
-          if (cs < ce) {
-            const int lo = lower_bound_col(B.ci, cs, ce, tbase);
-            const int hi = lower_bound_col(B.ci, lo, ce, tend);
-            s = lo;
-            len = hi - lo;
+          const int r0 = sp.rr[k], r1 = sp.rr[k + 1] - 1;  // runs without the sentinel
+          const int j = lower_bound_run(sp.runs, r0, r1, tw);
+          if (j < r1) {
+            const int2 cur = sp.runs[j];
+            if (cur.x == tw) {
+              s = cur.y;
+              len = sp.runs[j + 1].y - cur.y;
+            }
           }
         }
         win.segments(B, bv, s, len, a, tbase);
       }
       const int ncols = min(W, cmx - tbase + 1);
-      const long long n = win.emit(tbase, (ncols + 511) & ~511, out0, out_end, c_ci, c_v);
+      const int n = win.emit(tbase, ncols, out0, out_end, c_ci + rbeg, c_v + rbeg);
       if (lane == 0 && out0 + n != out_end) atomicOr(err, EB_INTERNAL);
       continue;
     }
@@ -272,99 +274,96 @@ k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
     const long long i = ri.row_begin + r;
     const int a0 = A.rp[i], a1 = A.rp[i + 1], nA = a1 - a0;
     const int cmx = ri.cmax[r];
-    const long long out_beg = c_rp[r], out_end = c_rp[r + 1];
-    long long out = out_beg;
+    const long long rbeg = c_rp[r];
+    const int out_end = (int)(c_rp[r + 1] - rbeg);
+    int32_t* const rci = c_ci + rbeg;
+    T* const rcv = c_v + rbeg;
+    int out = 0;
     if (nA <= 32 * NW_SLOTS) {
+      // cursor per nonzero: run index j, its window id and segment [s0, s1)
       const int nslots = (nA + 31) >> 5;
-      int cur[NW_SLOTS], end[NW_SLOTS], nx[NW_SLOTS];
+      int rj[NW_SLOTS], wid[NW_SLOTS], s0[NW_SLOTS], s1[NW_SLOTS];
       T a[NW_SLOTS];
       int mn = INT_MAX;
 #pragma unroll
       for (int q = 0; q < NW_SLOTS; ++q) {
-        cur[q] = 0; end[q] = 0; nx[q] = INT_MAX; a[q] = T(0);
+        rj[q] = 0; wid[q] = INT_MAX; s0[q] = 0; s1[q] = 0; a[q] = T(0);
         if (q < nslots) {
           const int e = a0 + q * 32 + lane;
           if (e < a1) {
             const int k = A.ci[e];
             a[q] = av[e];
-            cur[q] = B.rp[k];
-            end[q] = B.rp[k + 1];
-            nx[q] = cur[q] < end[q] ? B.ci[cur[q]] : INT_MAX;
+            rj[q] = sp.rr[k];
+            const int2 c0 = sp.runs[rj[q]];
+            wid[q] = c0.x;
+            s0[q] = c0.y;
+            if (c0.x != INT_MAX) s1[q] = sp.runs[rj[q] + 1].y;  // empty rows hold only the sentinel
           }
-          mn = min(mn, nx[q]);
+          mn = min(mn, wid[q]);
         }
       }
-      int base = warp_min(mn);
-      while (base != INT_MAX) {
-        const int wend = (int)min((long long)base + W, (long long)INT_MAX);
+      int w = warp_min(mn);
+      while (w != INT_MAX) {
+        const int base = w << WSHIFT;
         mn = INT_MAX;
 #pragma unroll
         for (int q = 0; q < NW_SLOTS; ++q) {
           if (q < nslots) {
-            int s = cur[q], len = 0;
-            if (nx[q] < wend) {
-              int seg = end[q], nn = INT_MAX;
-              if (B.ci[end[q] - 1] >= wend) {
-                seg = lower_bound_col(B.ci, cur[q] + 1, end[q] - 1, wend);
-                nn = B.ci[seg];
-              }
-              len = seg - cur[q];
-              cur[q] = seg;
-              nx[q] = nn;
+            const bool act = wid[q] == w;
+            win.segments(B, bv, s0[q], act ? s1[q] - s0[q] : 0, a[q], base);
+            if (act) {  // advance to the next run of this B row
+              ++rj[q];
+              const int2 nx = sp.runs[rj[q]];
+              wid[q] = nx.x;
+              s0[q] = nx.y;
+              if (nx.x != INT_MAX) s1[q] = sp.runs[rj[q] + 1].y;
             }
-            win.segments(B, bv, s, len, a[q], base);
-            mn = min(mn, nx[q]);
+            mn = min(mn, wid[q]);
           }
         }
         const int ncols = min(W, cmx - base + 1);
-        out += win.emit(base, (ncols + 511) & ~511, out, out_end, c_ci, c_v);
-        base = warp_min(mn);
+        out += win.emit(base, ncols, out, out_end, rci, rcv);
+        w = warp_min(mn);
       }
     } else {
-      // cursors in global arrays parallel to A's nonzeros (one warp per row)
+      // run cursors in global arrays parallel to A's nonzeros (one warp per row)
       int mn = INT_MAX;
       for (int e = a0 + lane; e < a1; e += 32) {
         const int k = A.ci[e];
-        const int c0 = B.rp[k], c1 = B.rp[k + 1];
-        gcur[e] = c0;
-        const int v = c0 < c1 ? B.ci[c0] : INT_MAX;
+        const int j = sp.rr[k];
+        gcur[e] = j;
+        const int v = sp.runs[j].x;
         gnxt[e] = v;
         mn = min(mn, v);
       }
-      int base = warp_min(mn);
-      while (base != INT_MAX) {
-        const int wend = (int)min((long long)base + W, (long long)INT_MAX);
+      int w = warp_min(mn);
+      while (w != INT_MAX) {
+        const int base = w << WSHIFT;
         mn = INT_MAX;
         for (int e0 = a0; e0 < a1; e0 += 32) {
           const int e = e0 + lane;
           int s = 0, len = 0;
           T av_e = T(0);
           if (e < a1) {
-            const int nxe = gnxt[e];
-            if (nxe < wend) {
-              const int k = A.ci[e];
-              const int c1 = B.rp[k + 1];
-              const int c0 = gcur[e];
+            const int we = gnxt[e];
+            if (we == w) {
+              const int j = gcur[e];
+              const int2 c0 = sp.runs[j], c1 = sp.runs[j + 1];
               av_e = av[e];
-              int seg = c1, nn = INT_MAX;
-              if (B.ci[c1 - 1] >= wend) {
-                seg = lower_bound_col(B.ci, c0 + 1, c1 - 1, wend);
-                nn = B.ci[seg];
-              }
-              s = c0;
-              len = seg - c0;
-              gcur[e] = seg;
-              gnxt[e] = nn;
-              mn = min(mn, nn);
+              s = c0.y;
+              len = c1.y - c0.y;
+              gcur[e] = j + 1;
+              gnxt[e] = c1.x;
+              mn = min(mn, c1.x);
             } else {
-              mn = min(mn, nxe);
+              mn = min(mn, we);
             }
           }
           win.segments(B, bv, s, len, av_e, base);
         }
         const int ncols = min(W, cmx - base + 1);
-        out += win.emit(base, (ncols + 511) & ~511, out, out_end, c_ci, c_v);
-        base = warp_min(mn);
+        out += win.emit(base, ncols, out, out_end, rci, rcv);
+        w = warp_min(mn);
       }
     }
     if (lane == 0 && out != out_end) atomicOr(err, EB_INTERNAL);

@@ -233,7 +233,7 @@ __device__ __forceinline__ void bit_insert(uint32_t* bits, int j, int W, uint32_
 constexpr int SYM_MIN_FINE = 1024;
 
 template <int W, int GW, int WF = SYM_MIN_FINE>
-constexpr size_t sym_group_bytes() {
+__host__ __device__ constexpr size_t sym_group_bytes() {
   return (((size_t)(W / 32) * 4 + (size_t)GW * 8 + (size_t)(W / WF + 2) * 4) + 15) & ~(size_t)15;
 }
 

@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const int32_t* __r
 
 // One block: exclusive scan of the tile sums in place, total to nnz_c.
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_partials(long long* __restrict__ part, long long ntiles,
-                                                               DevStats* st, int32_t* c_rp, long long m) {
+                                                               DevStats* st, int32_t* c_rp, long long m,
+                                                               long long* total_out) {
   __shared__ long long s_carry;
   __shared__ long long s_tot;
   if (threadIdx.x == 0) s_carry = 0;
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_partials(long long* __res
   }
   if (threadIdx.x == 0) {
     const long long total = s_carry;
-    st->nnz_c = total;
+    *total_out = total;
     if (total >= (1ll << 31)) atomicOr(&st->err, EB_OVERFLOW);
     c_rp[m] = (int32_t)(total < (1ll << 31) ? total : 0);
   }
@@ -101,14 +102,15 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(int32_t* __restrict_
   }
 }
 
-cudaError_t launch_scan(const LaunchCtx& c, int32_t* c_rp, long long m, long long* part) {
+cudaError_t launch_scan(const LaunchCtx& c, int32_t* c_rp, long long m, long long* part, long long* total_out) {
+  if (!total_out) total_out = &c.st->nnz_c;
   const long long ntiles = (m + SCAN_TILE - 1) / SCAN_TILE;
   timer_mark(c, T_SCAN, 0);
   if (ntiles > 0) {
     k_scan_reduce<<<(unsigned)ntiles, SCAN_THREADS, 0, c.stream>>>(c_rp, m, part);
     count_launch(c);
   }
-  k_scan_partials<<<1, SCAN_THREADS, 0, c.stream>>>(part, ntiles, c.st, c_rp, m);
+  k_scan_partials<<<1, SCAN_THREADS, 0, c.stream>>>(part, ntiles, c.st, c_rp, m, total_out);
   count_launch(c);
   if (ntiles > 0) {
     k_scan_down<<<(unsigned)ntiles, SCAN_THREADS, 0, c.stream>>>(c_rp, m, part);
