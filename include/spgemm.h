@@ -88,7 +88,9 @@ typedef struct spgemm_opts {
   int32_t split_min;   /* rows with more products than this are split into column
                           tiles of window_warp columns, processed independently
                           (0: default 131072; -1: never split) */
-  int32_t reserved[6];
+  int32_t backward;    /* nonzero: the plan also keeps the transpose of A's structure,
+                          which spgemm_backward needs (more workspace) */
+  int32_t reserved[5];
 } spgemm_opts;
 
 typedef struct spgemm_plan spgemm_plan;
@@ -163,6 +165,40 @@ spgemm_status spgemm_plan_launches(spgemm_plan* plan, int64_t* launches);
 
 /* Blocks on `stream` and returns the device error word as a status. */
 spgemm_status spgemm_plan_check(spgemm_plan* plan, spgemm_stream_t stream);
+
+/* Adjoint of C = A*B for a scalar loss with gradient dC on C's pattern
+ * (for L = sum W .* C, dC = W):
+ *   dA(i,k) = sum_j dC(i,j) * B(k,j)  on pattern(A)   -- (dC * B^T) sampled on A
+ *   dB(k,j) = sum_i A(i,k) * dC(i,j)  on pattern(B)   -- (A^T * dC) sampled on B
+ * The plan must have been made with opts.backward set and spgemm_symbolic
+ * called; c_row_ptr / c_col_idx are C's structure from this plan, dc_vals
+ * its gradient values (plan dtype).  da_vals (aligned with A's col_idx, all
+ * of A's nonzeros; entries of rows outside the plan's row range are left
+ * untouched) and db_vals (aligned with B's col_idx; sums over the plan's
+ * rows only) are overwritten; either may be NULL to skip it.  Each output is
+ * one sequential fused multiply-add chain, so the result is deterministic.
+ * Does not block, allocates nothing. */
+spgemm_status spgemm_backward(spgemm_plan* plan, const void* a_vals, const void* b_vals,
+                              const int32_t* c_row_ptr, const int32_t* c_col_idx,
+                              const void* dc_vals, void* da_vals, void* db_vals,
+                              spgemm_stream_t stream);
+
+/* Device workspace bytes for spgemm_transpose of an nrows x ncols matrix
+ * with nnz entries (host only). */
+spgemm_status spgemm_transpose_workspace_size(int64_t nrows, int64_t ncols, int64_t nnz, size_t* bytes);
+
+/* M^T in CSR (Sec. 2.1: M's CSC form): t_row_ptr (ncols+1 entries),
+ * t_col_idx (nnz; each row ascending), t_vals (nnz values of `dtype`, or NULL
+ * for structure only), t_src (nnz source positions in M, or NULL), so that
+ * t_vals[q] = M.vals[t_src[q]].  Column indices of M must be in range.
+ * Does not block; spgemm_transpose_check reads the error word. */
+spgemm_status spgemm_transpose(const spgemm_csr* M, int32_t dtype, int32_t* t_row_ptr, int32_t* t_col_idx,
+                               void* t_vals, int32_t* t_src, void* workspace, size_t workspace_bytes,
+                               spgemm_stream_t stream);
+
+/* Blocks on `stream` and reports an error recorded by spgemm_transpose in
+ * this workspace (a column index out of range). */
+spgemm_status spgemm_transpose_check(void* workspace, spgemm_stream_t stream);
 
 /* Frees the plan (host memory only).  NULL is allowed. */
 void spgemm_plan_destroy(spgemm_plan* plan);

@@ -43,7 +43,7 @@ class spgemm_opts(ctypes.Structure):
                 ("warp_max", ctypes.c_int32), ("force_path", ctypes.c_int32),
                 ("hash_max", ctypes.c_int32), ("window_warp", ctypes.c_int32),
                 ("window_block", ctypes.c_int32), ("split_min", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("backward", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 _lib = None
@@ -67,6 +67,12 @@ _SIG = {
     "spgemm_plan_kernel_times": ([_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int], ctypes.c_int),
     "spgemm_plan_launches": ([_P, _I64P], ctypes.c_int),
     "spgemm_plan_destroy": ([_P], None),
+    "spgemm_backward": ([_P, _P, _P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
+    "spgemm_transpose_workspace_size": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "spgemm_transpose": ([ctypes.POINTER(spgemm_csr), ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_size_t, _P],
+                         ctypes.c_int),
+    "spgemm_transpose_check": ([_P, _P], ctypes.c_int),
 }
 
 
@@ -173,3 +179,26 @@ def spgemm_plan_launches(plan: int) -> int:
 def spgemm_plan_destroy(plan: int) -> None:
     if plan:
         lib().spgemm_plan_destroy(_P(plan))
+
+
+def spgemm_backward(plan: int, a_vals: int, b_vals: int, c_row_ptr: int, c_col_idx: int, dc_vals: int,
+                    da_vals: int, db_vals: int, stream: int) -> None:
+    _check(lib().spgemm_backward(_P(plan), _P(a_vals), _P(b_vals), _P(c_row_ptr), _P(c_col_idx), _P(dc_vals),
+                                 _P(da_vals), _P(db_vals), _P(stream)), "spgemm_backward")
+
+
+def spgemm_transpose_workspace_size(nrows: int, ncols: int, nnz: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().spgemm_transpose_workspace_size(nrows, ncols, nnz, ctypes.byref(n)),
+           "spgemm_transpose_workspace_size")
+    return n.value
+
+
+def spgemm_transpose(M: spgemm_csr, dtype: int, t_row_ptr: int, t_col_idx: int, t_vals: int, t_src: int,
+                     workspace: int, workspace_bytes: int, stream: int) -> None:
+    _check(lib().spgemm_transpose(ctypes.byref(M), dtype, _P(t_row_ptr), _P(t_col_idx), _P(t_vals), _P(t_src),
+                                  _P(workspace), ctypes.c_size_t(workspace_bytes), _P(stream)), "spgemm_transpose")
+
+
+def spgemm_transpose_check(workspace: int, stream: int) -> None:
+    _check(lib().spgemm_transpose_check(_P(workspace), _P(stream)), "spgemm_transpose_check")

@@ -62,7 +62,7 @@ def _stream_handle(stream=None) -> int:
 
 
 def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1, warp_max=0,
-              window_warp=0, window_block=0, split_min=0) -> nat.spgemm_opts:
+              window_warp=0, window_block=0, split_min=0, backward=False) -> nat.spgemm_opts:
     o = nat.spgemm_opts_default()
     o.dtype = _DT[dtype]
     o.validate = 1 if validate else 0
@@ -73,6 +73,7 @@ def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1
     o.window_warp = int(window_warp)
     o.window_block = int(window_block)
     o.split_min = int(split_min)
+    o.backward = 1 if backward else 0
     return o
 
 
@@ -97,6 +98,7 @@ class Plan:
                                          self.stream)
         self.nrows = (self.opts.row_end if self.opts.row_end >= 0 else A.nrows) - self.opts.row_begin
         self.row_ptr: Optional[torch.Tensor] = None
+        self.col_idx: Optional[torch.Tensor] = None
         self.nnz: Optional[int] = None
 
     def symbolic(self):
@@ -113,6 +115,7 @@ class Plan:
         if vals is None:
             vals = torch.empty(self.nnz, dtype=self.dtype, device=dev)
         assert a_vals.dtype == self.dtype and b_vals.dtype == self.dtype
+        self.col_idx = col_idx
         nat.spgemm_numeric(self.handle, a_vals.data_ptr() if a_vals.numel() else 0,
                            b_vals.data_ptr() if b_vals.numel() else 0, self.row_ptr.data_ptr(),
                            col_idx.data_ptr() if self.nnz else 0, vals.data_ptr() if self.nnz else 0,
@@ -147,3 +150,90 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, dtype=None, **opt_kw) -> DeviceCSR:
     ci, v = plan.numeric(A.vals, B.vals)
     plan.close()
     return DeviceCSR(plan.nrows, B.ncols, rp, ci, v)
+
+
+def transpose(M: DeviceCSR, want_src: bool = False, dtype=None, stream=None):
+    """M^T as a DeviceCSR (``spgemm_transpose``); with ``want_src`` also the
+    int32 source positions (t_vals[q] = M.vals[src[q]])."""
+    dev = M.row_ptr.device
+    dtype = dtype or (M.vals.dtype if M.vals is not None else torch.float64)
+    nbytes = nat.spgemm_transpose_workspace_size(M.nrows, M.ncols, M.nnz)
+    ws = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=dev)
+    t_rp = torch.empty(M.ncols + 1, dtype=torch.int32, device=dev)
+    t_ci = torch.empty(M.nnz, dtype=torch.int32, device=dev)
+    t_v = torch.empty(M.nnz, dtype=dtype, device=dev) if M.vals is not None else None
+    src = torch.empty(M.nnz, dtype=torch.int32, device=dev) if want_src else None
+    s = M.c_struct()
+    nat.spgemm_transpose(s, _DT[dtype], t_rp.data_ptr(), t_ci.data_ptr() if M.nnz else 0,
+                         t_v.data_ptr() if (t_v is not None and M.nnz) else 0,
+                         src.data_ptr() if (src is not None and M.nnz) else 0,
+                         ws.data_ptr(), nbytes, _stream_handle(stream))
+    nat.spgemm_transpose_check(ws.data_ptr(), _stream_handle(stream))
+    T = DeviceCSR(M.ncols, M.nrows, t_rp, t_ci, t_v)
+    return (T, src) if want_src else T
+
+
+def _plan_backward(self, a_vals, b_vals, dc_vals, need_a=True, need_b=True):
+    """(dA, dB) for dC on this plan's C pattern (``spgemm_backward``)."""
+    dev = self.workspace.device
+    da = torch.empty(self.A.nnz, dtype=self.dtype, device=dev) if need_a else None
+    db = torch.empty(self.B.nnz, dtype=self.dtype, device=dev) if need_b else None
+    nat.spgemm_backward(self.handle, a_vals.data_ptr() if a_vals.numel() else 0,
+                        b_vals.data_ptr() if b_vals.numel() else 0, self.row_ptr.data_ptr(),
+                        self.col_idx.data_ptr() if self.nnz else 0,
+                        dc_vals.data_ptr() if self.nnz else 0,
+                        da.data_ptr() if (da is not None and da.numel()) else 0,
+                        db.data_ptr() if (db is not None and db.numel()) else 0, self.stream)
+    return da, db
+
+
+Plan.backward = _plan_backward
+
+
+class SparseMatmul:
+    """Differentiable C = A*B for fixed patterns of A and B.
+
+    ``op = SparseMatmul(A, B)`` analyses the product once (with the
+    transpose of A's structure kept for the adjoint) and fixes C's pattern
+    (``op.row_ptr``, ``op.col_idx``).  ``op(a_vals, b_vals)`` returns C's
+    values and is differentiable in both arguments through
+    :class:`SpGEMMFn`, whose backward is ``spgemm_backward``.
+    """
+
+    def __init__(self, A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, **opt_kw):
+        self.plan = Plan(A, B, dtype=dtype, backward=True, **opt_kw)
+        self.row_ptr, self.nnz = self.plan.symbolic()
+        dev = A.row_ptr.device
+        # one numeric pass on zero values fixes C's column indices
+        za = torch.zeros(A.nnz, dtype=dtype, device=dev)
+        zb = torch.zeros(B.nnz, dtype=dtype, device=dev)
+        self.col_idx, _ = self.plan.numeric(za, zb)
+        self.dtype = dtype
+
+    def __call__(self, a_vals, b_vals):
+        return SpGEMMFn.apply(a_vals, b_vals, self)
+
+
+class SpGEMMFn(torch.autograd.Function):
+    """Values of C = A*B on the fixed pattern; backward gives
+    dA = (dC B^T) on pattern(A) and dB = (A^T dC) on pattern(B)."""
+
+    @staticmethod
+    def forward(ctx, a_vals, b_vals, op):
+        p = op.plan
+        vals = torch.empty(op.nnz, dtype=op.dtype, device=a_vals.device)
+        nat.spgemm_numeric(p.handle, a_vals.data_ptr() if a_vals.numel() else 0,
+                           b_vals.data_ptr() if b_vals.numel() else 0, op.row_ptr.data_ptr(),
+                           op.col_idx.data_ptr() if op.nnz else 0, vals.data_ptr() if op.nnz else 0, p.stream)
+        ctx.save_for_backward(a_vals, b_vals)
+        ctx.op = op
+        return vals
+
+    @staticmethod
+    def backward(ctx, dc):
+        a_vals, b_vals = ctx.saved_tensors
+        op = ctx.op
+        dc = dc.contiguous().to(op.dtype)
+        da, db = op.plan.backward(a_vals, b_vals, dc, need_a=ctx.needs_input_grad[0],
+                                  need_b=ctx.needs_input_grad[1])
+        return da, db, None

@@ -24,6 +24,10 @@ struct spgemm_plan {
   int32_t* nxt = nullptr;
   long long* scan_part = nullptr;
   long long* runs_part = nullptr;
+  // transpose of A's structure (backward pass)
+  int32_t* at_rp = nullptr;
+  int32_t* at_ci = nullptr;
+  int32_t* at_src = nullptr;
   // host state
   sg::PathBins pb{};
   sg::Tuning tu{};
@@ -50,8 +54,19 @@ constexpr size_t ALIGN = 256;
 inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 
 struct Layout {
-  size_t st, prod, cmin, cmax, rows, cursor, nxt, scan, rr, runs, runs_part, hcnt, total;
+  size_t st, prod, cmin, cmax, rows, cursor, nxt, scan, rr, runs, runs_part, hcnt;
+  size_t at_rp, at_ci, at_src, at_fill, at_tmp, at_part;  // opts.backward only
+  size_t total;
 };
+
+// Workspace of a transpose of an m x n matrix with nnz entries, at offset
+// `off`; returns the end offset.
+size_t transpose_layout(size_t off, long long n, long long nnz, size_t* fill, size_t* tmp, size_t* part) {
+  *fill = off; off = align_up(off + sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  *tmp = off; off = align_up(off + 2 * sizeof(int32_t) * (size_t)nnz);
+  *part = off; off = align_up(off + sizeof(long long) * sg::scan_partials_count(n));
+  return off;
+}
 
 // Window geometry and split capacity from the options and B's width (see
 // sg::SplitInfo).  *hcnt_entries is 0 when no row is split.
@@ -101,6 +116,12 @@ Layout layout_for(const spgemm_opts& o, long long mloc, long long nnz_a, long lo
   L.runs = off; off = align_up(off + sizeof(int2) * (size_t)(nnz_b + nrows_b));
   L.runs_part = off; off = align_up(off + sizeof(long long) * sg::scan_partials_count(nrows_b));
   L.hcnt = off; off = align_up(off + sizeof(int32_t) * nh);
+  if (o.backward) {
+    L.at_rp = off; off = align_up(off + sizeof(int32_t) * (size_t)(nrows_b + 1));
+    L.at_ci = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
+    L.at_src = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
+    off = transpose_layout(off, nrows_b, nnz_a, &L.at_fill, &L.at_tmp, &L.at_part);
+  }
   L.total = off;
   return L;
 }
@@ -210,6 +231,7 @@ void spgemm_opts_default(spgemm_opts* o) {
   o->window_warp = 0;
   o->window_block = 0;
   o->split_min = 0;
+  o->backward = 0;
 }
 
 const char* spgemm_status_string(spgemm_status s) {
@@ -302,6 +324,14 @@ spgemm_status spgemm_analyse(const spgemm_csr* A, const spgemm_csr* B, const spg
   }
   if (e == cudaSuccess) e = sg::launch_analyse(c, p->A, p->B, p->row_begin, p->mloc, p->prod, p->cmin, p->cmax, p->rows);
   if (e == cudaSuccess) e = sg::launch_runs(c, p->B, p->sp, p->runs_part);
+  if (e == cudaSuccess && o.backward) {
+    p->at_rp = (int32_t*)(p->ws + L.at_rp);
+    p->at_ci = (int32_t*)(p->ws + L.at_ci);
+    p->at_src = (int32_t*)(p->ws + L.at_src);
+    int32_t* tmp = (int32_t*)(p->ws + L.at_tmp);
+    e = sg::launch_transpose(c, A->nrows, A->ncols, A->nnz, A->row_ptr, A->col_idx, p->at_rp, p->at_ci, p->at_src,
+                             (int32_t*)(p->ws + L.at_fill), tmp, tmp + A->nnz, (long long*)(p->ws + L.at_part));
+  }
   if (e != cudaSuccess) { delete p; return SPGEMM_ERR_CUDA; }
   *plan = p;
   return SPGEMM_OK;
@@ -387,6 +417,79 @@ spgemm_status spgemm_plan_launches(spgemm_plan* p, int64_t* launches) {
   if (!p || !launches) return SPGEMM_ERR_INVALID_ARG;
   *launches = p->launches;
   return SPGEMM_OK;
+}
+
+spgemm_status spgemm_backward(spgemm_plan* p, const void* a_vals, const void* b_vals, const int32_t* c_row_ptr,
+                              const int32_t* c_col_idx, const void* dc_vals, void* da_vals, void* db_vals,
+                              spgemm_stream_t stream) {
+  if (!p) return SPGEMM_ERR_INVALID_ARG;
+  if (!p->symbolic_done || !p->at_rp) return SPGEMM_ERR_NOT_READY;
+  if (!da_vals && !db_vals) return SPGEMM_OK;
+  if (!c_row_ptr || (p->nnz_c > 0 && (!c_col_idx || !dc_vals))) return SPGEMM_ERR_INVALID_ARG;
+  if ((da_vals && p->B.nnz > 0 && !b_vals) || (db_vals && p->A.nnz > 0 && !a_vals)) return SPGEMM_ERR_INVALID_ARG;
+  sg::LaunchCtx c = ctx_of(p, stream);
+  cudaError_t e = cudaSuccess;
+  // rows outside the plan's range keep their dA; zero nothing else
+  if (db_vals && p->B.nnz > 0)
+    e = cudaMemsetAsync(db_vals, 0, (size_t)p->B.nnz * (p->opts.dtype == SPGEMM_F32 ? 4 : 8), c.stream);
+  if (e == cudaSuccess)
+    e = sg::launch_backward(c, p->opts.dtype, p->A, p->B, p->row_begin, p->mloc, a_vals, b_vals, p->at_rp, p->at_ci,
+                            p->at_src, c_row_ptr, c_col_idx, dc_vals, da_vals, db_vals);
+  return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
+}
+
+spgemm_status spgemm_transpose_workspace_size(int64_t nrows, int64_t ncols, int64_t nnz, size_t* bytes) {
+  if (!bytes || nrows < 0 || ncols < 0 || nnz < 0) return SPGEMM_ERR_INVALID_ARG;
+  if (nnz >= (1ll << 31) || ncols >= (1ll << 31) - 1) return SPGEMM_ERR_INDEX_OVERFLOW;
+  size_t fill, tmp, part;
+  size_t off = align_up(sizeof(sg::DevStats));
+  off = align_up(off + sizeof(int32_t) * (size_t)nnz);  // source positions if the caller wants none
+  *bytes = transpose_layout(off, ncols, nnz, &fill, &tmp, &part);
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_transpose(const spgemm_csr* M, int32_t dtype, int32_t* t_row_ptr, int32_t* t_col_idx,
+                               void* t_vals, int32_t* t_src, void* workspace, size_t workspace_bytes,
+                               spgemm_stream_t stream) {
+  spgemm_status s;
+  if ((s = check_csr(M)) != SPGEMM_OK) return s;
+  if (!t_row_ptr || (M->nnz > 0 && !t_col_idx)) return SPGEMM_ERR_INVALID_ARG;
+  if (dtype != SPGEMM_F64 && dtype != SPGEMM_F32) return SPGEMM_ERR_INVALID_ARG;
+  if (t_vals && M->nnz > 0 && !M->vals) return SPGEMM_ERR_INVALID_ARG;
+  size_t need = 0;
+  if ((s = spgemm_transpose_workspace_size(M->nrows, M->ncols, M->nnz, &need)) != SPGEMM_OK) return s;
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace) % 16) return SPGEMM_ERR_WORKSPACE;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  unsigned char* ws = (unsigned char*)workspace;
+  sg::LaunchCtx c{};
+  c.stream = (cudaStream_t)stream;
+  c.nsm = sm_count_for(dev);
+  c.st = (sg::DevStats*)ws;
+  c.err = &c.st->err;
+  size_t off = align_up(sizeof(sg::DevStats));
+  int32_t* own_src = (int32_t*)(ws + off);
+  off = align_up(off + sizeof(int32_t) * (size_t)M->nnz);
+  size_t fill, tmp, part;
+  transpose_layout(off, M->ncols, M->nnz, &fill, &tmp, &part);
+  int32_t* src = t_src ? t_src : own_src;
+  int32_t* tmpp = (int32_t*)(ws + tmp);
+  cudaError_t e = cudaMemsetAsync(c.st, 0, sizeof(sg::DevStats), c.stream);
+  if (e == cudaSuccess)
+    e = sg::launch_transpose(c, M->nrows, M->ncols, M->nnz, M->row_ptr, M->col_idx, t_row_ptr, t_col_idx, src,
+                             (int32_t*)(ws + fill), tmpp, tmpp + M->nnz, (long long*)(ws + part));
+  if (e == cudaSuccess && t_vals) e = sg::launch_gather(c, dtype, M->vals, src, t_vals, M->nnz);
+  return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
+}
+
+spgemm_status spgemm_transpose_check(void* workspace, spgemm_stream_t stream) {
+  if (!workspace) return SPGEMM_ERR_INVALID_ARG;
+  uint32_t w = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemcpyAsync(&w, &((sg::DevStats*)workspace)->err, sizeof(w), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return SPGEMM_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  return from_err_word(w);
 }
 
 void spgemm_plan_destroy(spgemm_plan* p) { delete p; }

@@ -43,6 +43,7 @@ struct DevStats {
   unsigned long long max_products;
   long long nnz_c;
   long long nruns;   // entries of B's window-run list
+  long long scratch_total;  // total of the transpose's prefix sum
   uint32_t err;
   uint32_t pad;
   int hist[NBINS];   // rows per bin
@@ -223,6 +224,15 @@ cudaError_t launch_numeric(const LaunchCtx& c, const Csr& A, const Csr& B, const
                            const void* av, const void* bv, int32_t* cursor, int32_t* nxt,
                            const int32_t* c_rp, int32_t* c_ci, void* c_v,
                            const int* path_rows /* host, may be null */);
+
+cudaError_t launch_transpose(const LaunchCtx& c, long long m, long long n, long long nnz, const int32_t* rp,
+                             const int32_t* ci, int32_t* t_rp, int32_t* t_ci, int32_t* t_src, int32_t* fill,
+                             int32_t* tmp_ci, int32_t* tmp_src, long long* partials);
+cudaError_t launch_gather(const LaunchCtx& c, int dtype, const void* v, const int32_t* src, void* out, long long nnz);
+cudaError_t launch_backward(const LaunchCtx& c, int dtype, const Csr& A, const Csr& B, long long row_begin,
+                            long long mloc, const void* av, const void* bv, const int32_t* t_rp,
+                            const int32_t* t_ci, const int32_t* t_src, const int32_t* c_rp,
+                            const int32_t* c_ci, const void* dc, void* da, void* db);
 
 // Number of split (heavy) rows: the leading rows of bins >= heavy_bin,
 // capped at hcap.
