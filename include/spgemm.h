@@ -203,6 +203,50 @@ spgemm_status spgemm_transpose_check(void* workspace, spgemm_stream_t stream);
 /* Frees the plan (host memory only).  NULL is allowed. */
 void spgemm_plan_destroy(spgemm_plan* plan);
 
+/* ------------------------------------------------------------------ batch
+ * Many independent products C_i = A_i * B_i (i < n) computed together: the
+ * instances are stacked into one block-diagonal product, so each pass is one
+ * persistent launch per path over a global work list of all instances' rows
+ * (largest rows first).  The stacked C is returned in one CSR: instance i
+ * owns the rows [r_i, r_i + A_i.nrows) with r_i = sum of the earlier
+ * A_j.nrows, and its column indices are its own (0 .. B_i.ncols-1).
+ * Counts over all instances (rows, nnz of A, nnz of B, nnz of C) must each
+ * fit int32 (split a larger batch into waves). */
+typedef struct spgemm_batch spgemm_batch;
+
+/* Device workspace bytes for a batch (host only). */
+spgemm_status spgemm_batch_workspace_size(int32_t n, const spgemm_csr* As, const spgemm_csr* Bs,
+                                          const spgemm_opts* opts, size_t* bytes);
+
+/* Creates the batch from n host descriptors whose pointers are device
+ * pointers; As[i].vals / Bs[i].vals are the value buffers that every later
+ * spgemm_batch_numeric reads (update them in place for new values).  Stacks
+ * the structure and analyses the stacked product on `stream`; does not block.
+ * All buffers must stay valid until spgemm_batch_destroy. */
+spgemm_status spgemm_batched(int32_t n, const spgemm_csr* As, const spgemm_csr* Bs, const spgemm_opts* opts,
+                             void* workspace, size_t workspace_bytes, spgemm_stream_t stream,
+                             spgemm_batch** batch);
+
+/* Rows of the stacked C (the length of c_row_ptr minus one). */
+spgemm_status spgemm_batch_rows(spgemm_batch* batch, int64_t* total_rows);
+
+/* Symbolic pass of all instances: writes the stacked row pointer and BLOCKS
+ * to return c_nnz[i] for each instance and c_nnz[n] = total (host array of
+ * n+1 entries). */
+spgemm_status spgemm_batch_symbolic(spgemm_batch* batch, int32_t* c_row_ptr, int64_t* c_nnz,
+                                    spgemm_stream_t stream);
+
+/* Numeric pass of all instances: gathers the instances' values, runs the
+ * stacked numeric pass, writes C's columns (per-instance numbering) and
+ * values.  Does not block and allocates nothing: capturable in a CUDA graph. */
+spgemm_status spgemm_batch_numeric(spgemm_batch* batch, const int32_t* c_row_ptr, int32_t* c_col_idx,
+                                   void* c_vals, spgemm_stream_t stream);
+
+/* The plan of the stacked product (statistics, timers, error word). */
+spgemm_plan* spgemm_batch_plan(spgemm_batch* batch);
+
+void spgemm_batch_destroy(spgemm_batch* batch);
+
 #ifdef __cplusplus
 }
 #endif

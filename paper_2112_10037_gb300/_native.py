@@ -73,6 +73,15 @@ _SIG = {
     "spgemm_transpose": ([ctypes.POINTER(spgemm_csr), ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_size_t, _P],
                          ctypes.c_int),
     "spgemm_transpose_check": ([_P, _P], ctypes.c_int),
+    "spgemm_batch_workspace_size": ([ctypes.c_int32, ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
+                                     ctypes.POINTER(spgemm_opts), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "spgemm_batched": ([ctypes.c_int32, ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
+                        ctypes.POINTER(spgemm_opts), _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "spgemm_batch_rows": ([_P, _I64P], ctypes.c_int),
+    "spgemm_batch_symbolic": ([_P, _P, _I64P, _P], ctypes.c_int),
+    "spgemm_batch_numeric": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "spgemm_batch_plan": ([_P], _P),
+    "spgemm_batch_destroy": ([_P], None),
 }
 
 
@@ -202,3 +211,47 @@ def spgemm_transpose(M: spgemm_csr, dtype: int, t_row_ptr: int, t_col_idx: int, 
 
 def spgemm_transpose_check(workspace: int, stream: int) -> None:
     _check(lib().spgemm_transpose_check(_P(workspace), _P(stream)), "spgemm_transpose_check")
+
+
+def spgemm_batch_workspace_size(As, Bs, opts: spgemm_opts) -> int:
+    n = len(As)
+    arrA, arrB = (spgemm_csr * max(n, 1))(*As), (spgemm_csr * max(n, 1))(*Bs)
+    out = ctypes.c_size_t(0)
+    _check(lib().spgemm_batch_workspace_size(n, arrA, arrB, ctypes.byref(opts), ctypes.byref(out)),
+           "spgemm_batch_workspace_size")
+    return out.value
+
+
+def spgemm_batched(As, Bs, opts: spgemm_opts, workspace: int, workspace_bytes: int, stream: int) -> int:
+    n = len(As)
+    arrA, arrB = (spgemm_csr * max(n, 1))(*As), (spgemm_csr * max(n, 1))(*Bs)
+    h = _P(None)
+    _check(lib().spgemm_batched(n, arrA, arrB, ctypes.byref(opts), _P(workspace), ctypes.c_size_t(workspace_bytes),
+                                _P(stream), ctypes.byref(h)), "spgemm_batched")
+    return h.value
+
+
+def spgemm_batch_rows(batch: int) -> int:
+    r = ctypes.c_int64(0)
+    _check(lib().spgemm_batch_rows(_P(batch), ctypes.byref(r)), "spgemm_batch_rows")
+    return r.value
+
+
+def spgemm_batch_symbolic(batch: int, n: int, c_row_ptr: int, stream: int):
+    nnz = (ctypes.c_int64 * (n + 1))()
+    _check(lib().spgemm_batch_symbolic(_P(batch), _P(c_row_ptr), nnz, _P(stream)), "spgemm_batch_symbolic")
+    return list(nnz)
+
+
+def spgemm_batch_numeric(batch: int, c_row_ptr: int, c_col_idx: int, c_vals: int, stream: int) -> None:
+    _check(lib().spgemm_batch_numeric(_P(batch), _P(c_row_ptr), _P(c_col_idx), _P(c_vals), _P(stream)),
+           "spgemm_batch_numeric")
+
+
+def spgemm_batch_plan(batch: int) -> int:
+    return lib().spgemm_batch_plan(_P(batch))
+
+
+def spgemm_batch_destroy(batch: int) -> None:
+    if batch:
+        lib().spgemm_batch_destroy(_P(batch))

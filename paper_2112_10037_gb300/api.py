@@ -237,3 +237,142 @@ class SpGEMMFn(torch.autograd.Function):
         da, db = op.plan.backward(a_vals, b_vals, dc, need_a=ctx.needs_input_grad[0],
                                   need_b=ctx.needs_input_grad[1])
         return da, db, None
+
+
+class Batch:
+    """Independent products C_i = A_i * B_i computed together
+    (``spgemm_batched``): one analysis and one persistent launch per pass
+    over all instances' rows.
+
+    ``symbolic()`` sizes every C_i; ``numeric()`` fills the stacked C from
+    the current values of every A_i / B_i (update ``A_i.vals`` in place for
+    new values); ``results()`` returns per-instance DeviceCSR views.
+    ``capture()`` records the numeric pass in a CUDA graph; ``replay()``
+    launches it.
+    """
+
+    def __init__(self, pairs, dtype=torch.float64, stream=None, **opt_kw):
+        self.pairs = list(pairs)
+        self.dtype = dtype
+        self.opts = make_opts(dtype=dtype, **opt_kw)
+        self._as = [a.c_struct() for a, _ in self.pairs]
+        self._bs = [b.c_struct() for _, b in self.pairs]
+        for s_, (a, b) in zip(self._as, self.pairs):
+            s_.vals = a.vals.data_ptr() if a.nnz else 0
+        for s_, (a, b) in zip(self._bs, self.pairs):
+            s_.vals = b.vals.data_ptr() if b.nnz else 0
+        dev = self.pairs[0][0].row_ptr.device if self.pairs else torch.device("cuda")
+        nbytes = nat.spgemm_batch_workspace_size(self._as, self._bs, self.opts)
+        self.workspace = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=dev)
+        self.stream = _stream_handle(stream)
+        self.handle = nat.spgemm_batched(self._as, self._bs, self.opts, self.workspace.data_ptr(), nbytes,
+                                         self.stream)
+        self.rows = nat.spgemm_batch_rows(self.handle)
+        self.device = dev
+        self.row_ptr = self.col_idx = self.vals = None
+        self.nnz = None
+        self.graph = None
+
+    def symbolic(self):
+        self.row_ptr = torch.empty(self.rows + 1, dtype=torch.int32, device=self.device)
+        self.nnz = nat.spgemm_batch_symbolic(self.handle, len(self.pairs), self.row_ptr.data_ptr(), self.stream)
+        total = self.nnz[-1]
+        self.col_idx = torch.empty(total, dtype=torch.int32, device=self.device)
+        self.vals = torch.empty(total, dtype=self.dtype, device=self.device)
+        return self.nnz
+
+    def numeric(self):
+        if self.row_ptr is None:
+            self.symbolic()
+        nat.spgemm_batch_numeric(self.handle, self.row_ptr.data_ptr(),
+                                 self.col_idx.data_ptr() if self.nnz[-1] else 0,
+                                 self.vals.data_ptr() if self.nnz[-1] else 0, self.stream)
+
+    def capture(self):
+        """Record numeric() in a CUDA graph (after one eager numeric())."""
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            saved = self.stream
+            self.stream = int(s.cuda_stream)
+            with torch.cuda.graph(g, stream=s):
+                self.numeric()
+            self.stream = saved
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+
+    def results(self):
+        out, r0, e0 = [], 0, 0
+        for (a, b), n in zip(self.pairs, self.nnz[:-1]):
+            rp = self.row_ptr[r0:r0 + a.nrows + 1] - e0
+            out.append(DeviceCSR(a.nrows, b.ncols, rp, self.col_idx[e0:e0 + n], self.vals[e0:e0 + n]))
+            r0 += a.nrows
+            e0 += n
+        return out
+
+    def plan_handle(self):
+        return nat.spgemm_batch_plan(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            nat.spgemm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Galerkin:
+    """The Galerkin triple product A_c = P^T (A P) as a chain of two products.
+
+    Construction transposes P (``spgemm_transpose``, values included),
+    analyses A*P and R*(AP) with R = P^T, and runs both symbolic passes once
+    (the structure of A and P must then stay fixed).  ``numeric()``
+    recomputes A_c from the current values of A (P's values are those of
+    construction); ``capture()`` records both numeric passes in one CUDA
+    graph, ``replay()`` relaunches it.
+    """
+
+    def __init__(self, P: DeviceCSR, A: DeviceCSR, dtype=torch.float64, **opt_kw):
+        self.P, self.A, self.dtype = P, A, dtype
+        self.R, self.r_src = transpose(P, want_src=True, dtype=dtype)
+        self.plan_ap = Plan(A, P, dtype=dtype, **opt_kw)
+        self.ap_rp, ap_nnz = self.plan_ap.symbolic()
+        self.ap_ci, self.ap_v = self.plan_ap.numeric(A.vals, P.vals)
+        self.AP = DeviceCSR(A.nrows, P.ncols, self.ap_rp, self.ap_ci, self.ap_v)
+        self.plan_c = Plan(self.R, self.AP, dtype=dtype, **opt_kw)
+        self.c_rp, c_nnz = self.plan_c.symbolic()
+        self.c_ci, self.c_v = self.plan_c.numeric(self.R.vals, self.ap_v)
+        self.Ac = DeviceCSR(P.ncols, P.ncols, self.c_rp, self.c_ci, self.c_v)
+        self.graph = None
+
+    def numeric(self):
+        self.plan_ap.numeric(self.A.vals, self.P.vals, col_idx=self.ap_ci, vals=self.ap_v)
+        self.plan_c.numeric(self.R.vals, self.ap_v, col_idx=self.c_ci, vals=self.c_v)
+        return self.Ac
+
+    def capture(self):
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(device=self.A.row_ptr.device)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            saved = (self.plan_ap.stream, self.plan_c.stream)
+            self.plan_ap.stream = self.plan_c.stream = int(s.cuda_stream)
+            with torch.cuda.graph(g, stream=s):
+                self.numeric()
+            self.plan_ap.stream, self.plan_c.stream = saved
+        torch.cuda.current_stream().wait_stream(s)
+        self.graph = g
+        return g
+
+    def replay(self):
+        self.graph.replay()
+        return self.Ac

@@ -3,6 +3,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -493,5 +494,186 @@ spgemm_status spgemm_transpose_check(void* workspace, spgemm_stream_t stream) {
 }
 
 void spgemm_plan_destroy(spgemm_plan* p) { delete p; }
+
+}  // extern "C"
+
+struct spgemm_batch {
+  int n = 0;
+  int dtype = SPGEMM_F64;
+  long long rows = 0, ks = 0, ncols = 0, a_nnz = 0, b_nnz = 0;
+  std::vector<sg::BatchDesc> desc;
+  sg::BatchDesc* d_desc = nullptr;
+  int32_t *a_rp = nullptr, *a_ci = nullptr, *b_rp = nullptr, *b_ci = nullptr, *bounds = nullptr;
+  void *a_v = nullptr, *b_v = nullptr;
+  spgemm_plan* plan = nullptr;
+  std::vector<int32_t> host_bounds;
+  ~spgemm_batch() { spgemm_plan_destroy(plan); }
+};
+
+namespace {
+
+struct BatchLayout {
+  size_t desc, a_rp, a_ci, a_v, b_rp, b_ci, b_v, bounds, plan, total;
+  spgemm_csr A, B;  // stacked shapes (pointers unset)
+};
+
+spgemm_status batch_layout(int n, const spgemm_csr* As, const spgemm_csr* Bs, const spgemm_opts& o,
+                           BatchLayout* L, std::vector<sg::BatchDesc>* desc) {
+  if (n < 0 || (n > 0 && (!As || !Bs))) return SPGEMM_ERR_INVALID_ARG;
+  long long rows = 0, ks = 0, ncols = 0, an = 0, bn = 0;
+  if (desc) desc->resize((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    spgemm_status s;
+    if ((s = check_csr(&As[i])) != SPGEMM_OK) return s;
+    if ((s = check_csr(&Bs[i])) != SPGEMM_OK) return s;
+    if (As[i].ncols != Bs[i].nrows) return SPGEMM_ERR_DIM_MISMATCH;
+    if (desc) {
+      sg::BatchDesc& D = (*desc)[(size_t)i];
+      D.a_rp = As[i].row_ptr; D.a_ci = As[i].col_idx; D.a_v = As[i].vals;
+      D.b_rp = Bs[i].row_ptr; D.b_ci = Bs[i].col_idx; D.b_v = Bs[i].vals;
+      D.m = As[i].nrows; D.k = As[i].ncols; D.n = Bs[i].ncols;
+      D.a_nnz = As[i].nnz; D.b_nnz = Bs[i].nnz;
+      D.roff = rows; D.koff = ks; D.noff = ncols; D.aoff = an; D.boff = bn;
+    }
+    rows += As[i].nrows; ks += As[i].ncols; ncols += Bs[i].ncols; an += As[i].nnz; bn += Bs[i].nnz;
+  }
+  const long long lim = (1ll << 31) - 1;
+  if (rows >= lim || ks >= lim || ncols >= lim || an >= lim || bn >= lim) return SPGEMM_ERR_INDEX_OVERFLOW;
+  const size_t vb = o.dtype == SPGEMM_F32 ? 4 : 8;
+  size_t off = 0;
+  L->desc = off; off = align_up(off + sizeof(sg::BatchDesc) * (size_t)(n > 0 ? n : 1));
+  L->a_rp = off; off = align_up(off + sizeof(int32_t) * (size_t)(rows + 1));
+  L->a_ci = off; off = align_up(off + sizeof(int32_t) * (size_t)an);
+  L->a_v = off; off = align_up(off + vb * (size_t)an);
+  L->b_rp = off; off = align_up(off + sizeof(int32_t) * (size_t)(ks + 1));
+  L->b_ci = off; off = align_up(off + sizeof(int32_t) * (size_t)bn);
+  L->b_v = off; off = align_up(off + vb * (size_t)bn);
+  L->bounds = off; off = align_up(off + sizeof(int32_t) * (size_t)(n + 1));
+  L->plan = off;
+  L->A = spgemm_csr{rows, ks, an, nullptr, nullptr, nullptr};
+  L->B = spgemm_csr{ks, ncols, bn, nullptr, nullptr, nullptr};
+  // the inner plan's size depends only on the stacked shapes
+  L->A.row_ptr = (const int32_t*)16;
+  L->B.row_ptr = (const int32_t*)16;
+  if (an) L->A.col_idx = (const int32_t*)16;
+  if (bn) L->B.col_idx = (const int32_t*)16;
+  size_t pw = 0;
+  spgemm_status s = spgemm_workspace_size(&L->A, &L->B, &o, &pw);
+  if (s != SPGEMM_OK) return s;
+  L->total = align_up(off + pw);
+  return SPGEMM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+spgemm_status spgemm_batch_workspace_size(int32_t n, const spgemm_csr* As, const spgemm_csr* Bs,
+                                          const spgemm_opts* opts, size_t* bytes) {
+  if (!bytes) return SPGEMM_ERR_INVALID_ARG;
+  spgemm_opts o;
+  if (opts) o = *opts; else spgemm_opts_default(&o);
+  o.row_begin = 0;
+  o.row_end = -1;
+  BatchLayout L;
+  spgemm_status s = batch_layout(n, As, Bs, o, &L, nullptr);
+  if (s == SPGEMM_OK) *bytes = L.total;
+  return s;
+}
+
+spgemm_status spgemm_batched(int32_t n, const spgemm_csr* As, const spgemm_csr* Bs, const spgemm_opts* opts,
+                             void* workspace, size_t workspace_bytes, spgemm_stream_t stream,
+                             spgemm_batch** batch) {
+  if (!batch) return SPGEMM_ERR_INVALID_ARG;
+  *batch = nullptr;
+  spgemm_opts o;
+  if (opts) o = *opts; else spgemm_opts_default(&o);
+  if (o.dtype != SPGEMM_F64 && o.dtype != SPGEMM_F32) return SPGEMM_ERR_INVALID_ARG;
+  o.row_begin = 0;
+  o.row_end = -1;
+  o.backward = 0;
+  spgemm_batch* b = new (std::nothrow) spgemm_batch();
+  if (!b) return SPGEMM_ERR_INTERNAL;
+  BatchLayout L;
+  spgemm_status s = batch_layout(n, As, Bs, o, &L, &b->desc);
+  if (s != SPGEMM_OK) { delete b; return s; }
+  if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace) % 16) { delete b; return SPGEMM_ERR_WORKSPACE; }
+  for (int i = 0; i < n; ++i)
+    if ((As[i].nnz > 0 && !As[i].vals) || (Bs[i].nnz > 0 && !Bs[i].vals)) { delete b; return SPGEMM_ERR_INVALID_ARG; }
+  unsigned char* ws = (unsigned char*)workspace;
+  b->n = n;
+  b->dtype = o.dtype;
+  b->rows = L.A.nrows; b->ks = L.A.ncols; b->ncols = L.B.ncols; b->a_nnz = L.A.nnz; b->b_nnz = L.B.nnz;
+  b->d_desc = (sg::BatchDesc*)(ws + L.desc);
+  b->a_rp = (int32_t*)(ws + L.a_rp); b->a_ci = (int32_t*)(ws + L.a_ci); b->a_v = ws + L.a_v;
+  b->b_rp = (int32_t*)(ws + L.b_rp); b->b_ci = (int32_t*)(ws + L.b_ci); b->b_v = ws + L.b_v;
+  b->bounds = (int32_t*)(ws + L.bounds);
+  b->host_bounds.resize((size_t)n + 1);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { delete b; return SPGEMM_ERR_CUDA; }
+  sg::LaunchCtx c{};
+  c.stream = (cudaStream_t)stream;
+  c.nsm = sm_count_for(dev);
+  cudaError_t e = cudaSuccess;
+  if (n > 0)
+    e = cudaMemcpyAsync(b->d_desc, b->desc.data(), sizeof(sg::BatchDesc) * (size_t)n, cudaMemcpyHostToDevice, c.stream);
+  if (e == cudaSuccess)
+    e = sg::launch_stack_structure(c, n, b->d_desc, b->rows, b->ks, b->a_rp, b->a_ci, b->b_rp, b->b_ci, b->a_nnz,
+                                   b->b_nnz);
+  if (n == 0 && e == cudaSuccess) {
+    e = cudaMemsetAsync(b->a_rp, 0, sizeof(int32_t), c.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->b_rp, 0, sizeof(int32_t), c.stream);
+  }
+  if (e != cudaSuccess) { delete b; return SPGEMM_ERR_CUDA; }
+  spgemm_csr A = L.A, B = L.B;
+  A.row_ptr = b->a_rp; A.col_idx = b->a_nnz ? b->a_ci : nullptr; A.vals = b->a_v;
+  B.row_ptr = b->b_rp; B.col_idx = b->b_nnz ? b->b_ci : nullptr; B.vals = b->b_v;
+  s = spgemm_analyse(&A, &B, &o, ws + L.plan, workspace_bytes - L.plan, stream, &b->plan);
+  if (s != SPGEMM_OK) { delete b; return s; }
+  *batch = b;
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_batch_rows(spgemm_batch* b, int64_t* total_rows) {
+  if (!b || !total_rows) return SPGEMM_ERR_INVALID_ARG;
+  *total_rows = b->rows;
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_batch_symbolic(spgemm_batch* b, int32_t* c_row_ptr, int64_t* c_nnz, spgemm_stream_t stream) {
+  if (!b || !c_row_ptr || !c_nnz) return SPGEMM_ERR_INVALID_ARG;
+  int64_t total = 0;
+  spgemm_status s = spgemm_symbolic(b->plan, c_row_ptr, &total, stream);
+  if (s != SPGEMM_OK) return s;
+  if (b->n > 0) {
+    sg::LaunchCtx c = ctx_of(b->plan, stream);
+    if (sg::launch_batch_bounds(c, b->n, b->d_desc, c_row_ptr, b->rows, b->bounds) != cudaSuccess) return SPGEMM_ERR_CUDA;
+    if (cudaMemcpyAsync(b->host_bounds.data(), b->bounds, sizeof(int32_t) * (size_t)(b->n + 1), cudaMemcpyDeviceToHost,
+                        c.stream) != cudaSuccess)
+      return SPGEMM_ERR_CUDA;
+    if (cudaStreamSynchronize(c.stream) != cudaSuccess) return SPGEMM_ERR_CUDA;
+    for (int i = 0; i < b->n; ++i) c_nnz[i] = (int64_t)b->host_bounds[(size_t)i + 1] - b->host_bounds[(size_t)i];
+  }
+  c_nnz[b->n] = total;
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_batch_numeric(spgemm_batch* b, const int32_t* c_row_ptr, int32_t* c_col_idx, void* c_vals,
+                                   spgemm_stream_t stream) {
+  if (!b || !c_row_ptr) return SPGEMM_ERR_INVALID_ARG;
+  if (!b->plan->symbolic_done) return SPGEMM_ERR_NOT_READY;
+  if (b->plan->nnz_c == 0) return SPGEMM_OK;
+  if (!c_col_idx || !c_vals) return SPGEMM_ERR_INVALID_ARG;
+  sg::LaunchCtx c = ctx_of(b->plan, stream);
+  if (sg::launch_stack_values(c, b->n, b->dtype, b->d_desc, b->a_v, b->b_v) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  spgemm_status s = spgemm_numeric(b->plan, b->a_v, b->b_v, c_row_ptr, c_col_idx, c_vals, stream);
+  if (s != SPGEMM_OK) return s;
+  if (sg::launch_unstack_columns(c, b->n, b->d_desc, c_row_ptr, c_col_idx) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  return SPGEMM_OK;
+}
+
+spgemm_plan* spgemm_batch_plan(spgemm_batch* b) { return b ? b->plan : nullptr; }
+
+void spgemm_batch_destroy(spgemm_batch* b) { delete b; }
 
 }  // extern "C"

@@ -234,6 +234,26 @@ cudaError_t launch_backward(const LaunchCtx& c, int dtype, const Csr& A, const C
                             const int32_t* t_ci, const int32_t* t_src, const int32_t* c_rp,
                             const int32_t* c_ci, const void* dc, void* da, void* db);
 
+// One instance of a batched product (see batch.cu).
+struct BatchDesc {
+  const int32_t* a_rp;
+  const int32_t* a_ci;
+  const void* a_v;
+  const int32_t* b_rp;
+  const int32_t* b_ci;
+  const void* b_v;
+  long long m, k, n;     // A_i is m x k, B_i is k x n
+  long long a_nnz, b_nnz;
+  long long roff, koff, noff, aoff, boff;  // offsets in the stacked arrays
+};
+cudaError_t launch_stack_structure(const LaunchCtx& c, int n, const BatchDesc* d, long long total_rows,
+                                   long long total_k, int32_t* a_rp, int32_t* a_ci, int32_t* b_rp, int32_t* b_ci,
+                                   long long total_a_nnz, long long total_b_nnz);
+cudaError_t launch_stack_values(const LaunchCtx& c, int n, int dtype, const BatchDesc* d, void* a_v, void* b_v);
+cudaError_t launch_unstack_columns(const LaunchCtx& c, int n, const BatchDesc* d, const int32_t* c_rp, int32_t* c_ci);
+cudaError_t launch_batch_bounds(const LaunchCtx& c, int n, const BatchDesc* d, const int32_t* c_rp, long long total_rows,
+                                int32_t* out);
+
 // Number of split (heavy) rows: the leading rows of bins >= heavy_bin,
 // capped at hcap.
 __device__ __forceinline__ int split_rows(const DevStats* st, const SplitInfo& sp) {
