@@ -200,6 +200,27 @@ spgemm_status spgemm_transpose(const spgemm_csr* M, int32_t dtype, int32_t* t_ro
  * this workspace (a column index out of range). */
 spgemm_status spgemm_transpose_check(void* workspace, spgemm_stream_t stream);
 
+/* The same transpose as spgemm_transpose, for callers that cannot allocate
+ * device memory when they need it (for example code inside an allocator's
+ * out-of-memory path, code holding a lock the allocator also takes, or a
+ * service whose device memory is fixed at start-up): it takes no workspace
+ * and allocates nothing.  The paper has no counterpart; this is a library
+ * convenience.
+ *
+ * Its scratch is one fixed 8 MiB device array inside this library, present
+ * on every GPU that loads the library until the process exits.  Inputs whose
+ * scratch would exceed it are rejected with SPGEMM_ERR_WORKSPACE: the need
+ * is about 4*nnz (12*nnz when t_src is NULL) + 4*ncols + 8*ncols/4096 bytes
+ * plus a few hundred bytes of bookkeeping.  The first call on a device looks
+ * up the array's device address; make that first call before any stream
+ * capture.  All calls on a device share the array (each call clears what
+ * must start at zero), so calls whose GPU work can overlap -- on different
+ * streams without ordering -- race and must not be issued.  Errors found on
+ * the device are not reported by this call. */
+spgemm_status spgemm_transpose_noalloc(const spgemm_csr* M, int32_t dtype, int32_t* t_row_ptr,
+                                       int32_t* t_col_idx, void* t_vals, int32_t* t_src,
+                                       spgemm_stream_t stream);
+
 /* Frees the plan (host memory only).  NULL is allowed. */
 void spgemm_plan_destroy(spgemm_plan* plan);
 

@@ -73,6 +73,7 @@ _SIG = {
     "spgemm_transpose": ([ctypes.POINTER(spgemm_csr), ctypes.c_int32, _P, _P, _P, _P, _P, ctypes.c_size_t, _P],
                          ctypes.c_int),
     "spgemm_transpose_check": ([_P, _P], ctypes.c_int),
+    "spgemm_transpose_noalloc": ([ctypes.POINTER(spgemm_csr), ctypes.c_int32, _P, _P, _P, _P, _P], ctypes.c_int),
     "spgemm_batch_workspace_size": ([ctypes.c_int32, ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
                                      ctypes.POINTER(spgemm_opts), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "spgemm_batched": ([ctypes.c_int32, ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
@@ -255,3 +256,9 @@ def spgemm_batch_plan(batch: int) -> int:
 def spgemm_batch_destroy(batch: int) -> None:
     if batch:
         lib().spgemm_batch_destroy(_P(batch))
+
+
+def spgemm_transpose_noalloc(M: spgemm_csr, dtype: int, t_row_ptr: int, t_col_idx: int, t_vals: int, t_src: int,
+                             stream: int) -> None:
+    _check(lib().spgemm_transpose_noalloc(ctypes.byref(M), dtype, _P(t_row_ptr), _P(t_col_idx), _P(t_vals),
+                                          _P(t_src), _P(stream)), "spgemm_transpose_noalloc")
