@@ -400,13 +400,193 @@ def run_reference(args, A, B, desc):
     }
 
 
+# ------------------------------------------------- secondary workloads
+def _events_ms(fn, steps, stream):
+    import torch
+    ts = []
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.mean(ts)), ts
+
+
+def _base_line(metric, value, unit, args, ms, desc):
+    return {"metric": metric, "value": round(value, 3), "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator, no dataset)", "config": desc}
+
+
+def run_batched(args):
+    """512 independent uneven products: the stacked batch (one launch per
+    pass) against one-by-one calls, full pipeline and numeric-only (graph
+    replay of the batch vs a loop of per-instance numeric calls)."""
+    import torch
+    from paper_2112_10037_gb300 import api, build as bld, autotune as at
+    bld.build()
+    insts = list(gen.batched_instances(args.batch_count, scale_rows=args.batch_scale))
+    pairs, products = [], 0
+    for inst in insts:
+        dA = api.DeviceCSR.from_host(inst.A)
+        dB = dA if inst.B is inst.A else api.DeviceCSR.from_host(inst.B)
+        pairs.append((dA, dB))
+        products += int(row_products(inst.A, inst.B).sum())
+    stream = torch.cuda.current_stream()
+    opts = {}
+    if args.tune:
+        opts = at.autotune_batch(pairs)
+    def batched_full():
+        b = api.Batch(pairs, **opts)
+        b.symbolic()
+        b.numeric()
+        b.close()
+    def per_call_full():
+        for dA, dB in pairs:
+            pl = api.Plan(dA, dB, **opts)
+            pl.symbolic()
+            pl.numeric(dA.vals, dB.vals)
+            pl.close()
+    for _ in range(args.warmup):
+        batched_full()
+        per_call_full()
+    t_b, _ = _events_ms(batched_full, args.steps, stream)
+    t_p, _ = _events_ms(per_call_full, args.steps, stream)
+    # steady state: structure fixed, numeric only
+    batch = api.Batch(pairs, **opts)
+    batch.symbolic()
+    batch.numeric()
+    batch.capture()
+    plans = []
+    outs = []
+    for dA, dB in pairs:
+        pl = api.Plan(dA, dB, **opts)
+        pl.symbolic()
+        outs.append(pl.numeric(dA.vals, dB.vals))
+        plans.append(pl)
+    def loop_numeric():
+        for (dA, dB), pl, (ci, v) in zip(pairs, plans, outs):
+            pl.numeric(dA.vals, dB.vals, col_idx=ci, vals=v)
+    for _ in range(args.warmup):
+        batch.replay()
+        loop_numeric()
+    t_g, _ = _events_ms(batch.replay, args.steps, stream)
+    t_l, _ = _events_ms(loop_numeric, args.steps, stream)
+    gf = lambda t: 2.0 * products / (t / 1e3) / 1e9
+    desc = {"workload": "batched_%d_instances_scale%g" % (len(insts), args.batch_scale),
+            "instances": len(insts), "rows_total": int(sum(i.rows for i in insts)), "products": products,
+            "nnz_C": int(batch.nnz[-1]), "options": opts or "defaults",
+            "note": "rows log-uniform in [1024, 200000] x scale; half stencil squares, half random A*B"}
+    out = _base_line("SpGEMM GFLOP/s (2*products/s), batched", gf(t_b), "GFLOP/s", args, t_b, desc)
+    out["per_call_full_gflops"] = round(gf(t_p), 3)
+    out["batched_graph_numeric_gflops"] = round(gf(t_g), 3)
+    out["per_call_numeric_gflops"] = round(gf(t_l), 3)
+    out["speedup_full"] = round(t_p / t_b, 3)
+    out["speedup_numeric"] = round(t_l / t_g, 3)
+    return out
+
+
+def run_galerkin(args):
+    """P^T (A P), 3D 7-point 96^3 with 2x2x2 aggregation: both numeric
+    passes replayed from one CUDA graph, against two plain calls."""
+    import torch
+    from paper_2112_10037_gb300 import api, build as bld
+    bld.build()
+    A = gen.laplacian_3d(96)
+    P = gen.aggregation_3d(96)
+    dA, dP = api.DeviceCSR.from_host(A), api.DeviceCSR.from_host(P)
+    R = api.transpose(dP)
+    stream = torch.cuda.current_stream()
+    g = api.Galerkin(dP, dA)
+    g.capture()
+    p1 = int(row_products(A, P).sum())
+    APh = g.AP.to_host()
+    Rh = R.to_host()
+    p2 = int(row_products(Rh, APh).sum())
+    def plain():
+        AP = api.spgemm(dA, dP)
+        api.spgemm(R, AP)
+    for _ in range(args.warmup):
+        g.replay()
+        plain()
+    reps = max(args.steps, 20)
+    t_g, _ = _events_ms(g.replay, reps, stream)
+    t_p, _ = _events_ms(plain, args.steps, stream)
+    gf = lambda t: 2.0 * (p1 + p2) / (t / 1e3) / 1e9
+    # byte model of the two numeric passes (A, B rows touched, C written)
+    bytes_ap = A.nnz * 12 + A.nrows * 8 + P.nnz * 12 + P.nrows * 8 + APh.nnz * 12 + A.nrows * 8
+    bytes_c = Rh.nnz * 12 + Rh.nrows * 8 + APh.nnz * 12 + APh.nrows * 8 + g.Ac.nnz * 12 + Rh.nrows * 8
+    peak, kind = measured_hbm_peak()
+    achieved = (bytes_ap + bytes_c) / (t_g / 1e3) / 1e9
+    desc = {"workload": "galerkin_96cube_2x2x2", "products_AP": p1, "products_PtAP": p2,
+            "nnz_AP": int(APh.nnz), "nnz_Ac": int(g.Ac.nnz)}
+    out = _base_line("SpGEMM GFLOP/s (2*products/s), Galerkin chain graph replay", gf(t_g), "GFLOP/s", args,
+                     t_g, desc)
+    out["two_plain_calls_gflops"] = round(gf(t_p), 3)
+    out["two_plain_calls_ms"] = round(t_p, 4)
+    out["roofline"] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                       "frac": round(achieved / peak, 4), "peak_kind": kind,
+                       "algorithmic_bytes": int(bytes_ap + bytes_c), "kernel": "both numeric passes (graph)"}
+    return out
+
+
+def run_backward(args):
+    """C = A*B, A and B 65536^2 with 32 random columns per row: forward
+    (numeric) and backward (dA, dB) through the autograd Function, FP64 and
+    FP32."""
+    import torch
+    from paper_2112_10037_gb300 import api, build as bld
+    bld.build()
+    n = 65536
+    rng = np.random.default_rng(0)
+    A = gen.random_rows(n, n, np.full(n, 32), np.random.default_rng(0))
+    B = gen.random_rows(n, n, np.full(n, 32), np.random.default_rng(1))
+    products = int(row_products(A, B).sum())
+    stream = torch.cuda.current_stream()
+    res = {}
+    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        dA, dB = api.DeviceCSR.from_host(A, dtype=dt), api.DeviceCSR.from_host(B, dtype=dt)
+        op = api.SparseMatmul(dA, dB, dtype=dt)
+        W = torch.from_numpy(np.random.default_rng(2).standard_normal(op.nnz)).to(device="cuda", dtype=dt)
+        a = dA.vals.clone().requires_grad_(True)
+        b = dB.vals.clone().requires_grad_(True)
+        fwd = lambda: op(a.detach(), b.detach())
+        c = op(a, b)
+        def bwd():
+            a.grad = None
+            b.grad = None
+            torch.autograd.backward(c, W, retain_graph=True)
+        for _ in range(args.warmup):
+            fwd()
+            bwd()
+        t_f, _ = _events_ms(fwd, args.steps, stream)
+        t_b, _ = _events_ms(bwd, args.steps, stream)
+        res[name] = {"forward_ms": round(t_f, 4), "backward_ms": round(t_b, 4),
+                     "forward_gflops": round(2.0 * products / (t_f / 1e3) / 1e9, 2),
+                     "backward_gflops": round(4.0 * products / (t_b / 1e3) / 1e9, 2)}
+    desc = {"workload": "differentiation_65536sq_32perrow", "products": products}
+    out = _base_line("SpGEMM backward GFLOP/s (4*products/s)", res["f64"]["backward_gflops"], "GFLOP/s", args,
+                     res["f64"]["backward_ms"], desc)
+    out["f64"] = res["f64"]
+    out["f32"] = res["f32"]
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "lap2d", "stencil3d"])
+    ap.add_argument("--workload", default="rmat",
+                    choices=["rmat", "lap2d", "stencil3d", "batched", "galerkin", "backward"])
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-scale", type=float, default=0.1,
+                    help="row-count scale of the batched instances (1.0 = rows in [1024, 200000])")
+    ap.add_argument("--tune", action="store_true", help="autotune the options first (batched / rmat)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
@@ -416,6 +596,11 @@ def main():
             return
         A, B, desc = make_workload(args.workload)
         print(json.dumps(run_reference(args, A, B, desc)), flush=True)
+        return
+    if args.workload in ("batched", "galerkin", "backward"):
+        if rank == 0:
+            runner = {"batched": run_batched, "galerkin": run_galerkin, "backward": run_backward}[args.workload]
+            print(json.dumps(runner(args)), flush=True)
         return
     if world > 1:
         import torch
