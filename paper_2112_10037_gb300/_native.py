@@ -43,7 +43,8 @@ class spgemm_opts(ctypes.Structure):
                 ("warp_max", ctypes.c_int32), ("force_path", ctypes.c_int32),
                 ("hash_max", ctypes.c_int32), ("window_warp", ctypes.c_int32),
                 ("window_block", ctypes.c_int32), ("split_min", ctypes.c_int32),
-                ("backward", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("backward", ctypes.c_int32), ("num_block_min", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 _lib = None

@@ -69,11 +69,15 @@ size_t transpose_layout(size_t off, long long n, long long nnz, size_t* fill, si
   return off;
 }
 
+int numeric_block_bin(const spgemm_opts& o);
+
 // Window geometry and split capacity from the options and B's width (see
 // sg::SplitInfo).  *hcnt_entries is 0 when no row is split.
 void split_geometry(const spgemm_opts& o, int window, long long mloc, long long ncols_b, sg::SplitInfo* sp,
                     size_t* hcnt_entries) {
   sp->heavy_bin = sg::NBINS;
+  sp->hi_bin = numeric_block_bin(o) - 1;  // the warp kernel's last bin
+  if (sp->hi_bin > sg::NBINS - 1) sp->hi_bin = sg::NBINS - 1;
   sp->hcap = 0;
   sp->wf_shift = 0;
   while ((1 << sp->wf_shift) < window) ++sp->wf_shift;
@@ -81,6 +85,7 @@ void split_geometry(const spgemm_opts& o, int window, long long mloc, long long 
   *hcnt_entries = 0;
   if (o.split_min < 0 || o.force_path >= 0 || mloc <= 0 || sp->ntf < 2) return;
   const long long smin = o.split_min > 0 ? o.split_min : 131072;
+  if (sg::bin_of(smin) + 1 >= numeric_block_bin(o)) return;  // those rows use the block window
   long long cap = mloc < 16384 ? mloc : 16384;
   const long long lim = ((long long)1 << 24) / sp->ntf;
   if (cap > lim) cap = lim;
@@ -92,6 +97,17 @@ void split_geometry(const spgemm_opts& o, int window, long long mloc, long long 
   if (sp->heavy_bin >= sg::NBINS) { sp->heavy_bin = sg::NBINS; return; }
   sp->hcap = (int)cap;
   *hcnt_entries = (size_t)cap * (size_t)sp->ntf;
+}
+
+// First bin of rows whose numeric pass uses the block-wide window.
+int numeric_block_bin(const spgemm_opts& o) {
+  if (o.force_path == 1 || o.force_path == 3) return sg::NBINS;  // warp window only
+  if (o.force_path == 2) return 9;                                 // every row above the register sort
+  if (o.force_path == 4) return 1;                                 // every non-empty row
+  if (o.num_block_min < 0) return sg::NBINS;
+  const long long m = o.num_block_min > 0 ? o.num_block_min : 32768;
+  const int b = sg::bin_of(m) + 1;
+  return b < 9 ? 9 : b;
 }
 
 int numeric_window(const spgemm_opts& o) {
@@ -154,8 +170,9 @@ void choose_paths(const spgemm_opts& o, sg::PathBins* pb, sg::Tuning* tu) {
   const int last = sg::NBINS - 1;
   tu->warp_max = o.warp_max > 0 ? o.warp_max : 8192;
   tu->window_warp = numeric_window(o);
-  tu->window_block = 0;
+  tu->window_block = o.window_block == 16384 ? 16384 : 8192;
   tu->hash_max = 0;
+  tu->num_lo_block = numeric_block_bin(o);
   constexpr int TINY_HI = 8;  // register sort up to 128 products
   const int wb = sg::bin_of(tu->warp_max) < TINY_HI + 1 ? TINY_HI + 1 : sg::bin_of(tu->warp_max);
   for (int p = 0; p < sg::NPATHS; ++p) { pb->lo[p] = 1; pb->hi[p] = 0; }
@@ -233,6 +250,7 @@ void spgemm_opts_default(spgemm_opts* o) {
   o->window_block = 0;
   o->split_min = 0;
   o->backward = 0;
+  o->num_block_min = 0;
 }
 
 const char* spgemm_status_string(spgemm_status s) {

@@ -81,9 +81,10 @@ struct PathBins {
 // Tuning of the paths, fixed when the plan is made.
 struct Tuning {
   int window_warp;     // numeric window width (columns) of the warp accumulator
-  int window_block;    // unused by the numeric pass (kept for the option)
+  int window_block;    // numeric window width (columns) of the block accumulator
   int hash_max;        // largest P of the hash path (0: path disabled)
   int warp_max;        // largest P of the symbolic warp path
+  int num_lo_block;    // numeric bins >= this use the block kernel (NBINS: never)
 };
 
 // Window-run list of B: the numeric pass uses windows of 2^wf_shift columns
@@ -98,6 +99,7 @@ struct Tuning {
 // most hcap of them; row h of the list owns hcnt[h * ntf .. h * ntf + ntf).
 struct SplitInfo {
   int heavy_bin;      // NBINS disables splitting
+  int hi_bin;         // split rows are the rows of bins [heavy_bin, hi_bin]
   int hcap;
   int wf_shift;       // log2 of the window (= fine tile) width
   int ntf;            // windows per row: ceil(ncols(B) / width)
@@ -254,12 +256,15 @@ cudaError_t launch_unstack_columns(const LaunchCtx& c, int n, const BatchDesc* d
 cudaError_t launch_batch_bounds(const LaunchCtx& c, int n, const BatchDesc* d, const int32_t* c_rp, long long total_rows,
                                 int32_t* out);
 
-// Number of split (heavy) rows: the leading rows of bins >= heavy_bin,
-// capped at hcap.
-__device__ __forceinline__ int split_rows(const DevStats* st, const SplitInfo& sp) {
-  if (sp.heavy_bin >= NBINS) return 0;
-  int n = 0;
-  for (int b = sp.heavy_bin; b < NBINS; ++b) n += st->hist[b];
+// Split (heavy) rows: list positions [*hs, *hs + return value) -- the rows of
+// bins [heavy_bin, hi_bin], at most hcap of them; split row h of both passes
+// is list position *hs + h.
+__device__ __forceinline__ int split_rows(const DevStats* st, const SplitInfo& sp, int* hs) {
+  *hs = 0;
+  if (sp.heavy_bin >= NBINS || sp.hi_bin < sp.heavy_bin) return 0;
+  int he = 0;
+  bin_range(st, sp.heavy_bin, sp.hi_bin, hs, &he);
+  const int n = he - *hs;
   return n < sp.hcap ? n : sp.hcap;
 }
 

@@ -2,6 +2,7 @@
 #include <cstddef>
 
 #include "launch_util.cuh"
+#include "numblock.cuh"
 #include "numwarp.cuh"
 #include "rowpass.cuh"
 
@@ -33,6 +34,7 @@ static cudaError_t warp_num(const LaunchCtx& c, const Csr& A, const Csr& B, cons
   if (occ <= 0) return cudaErrorInvalidConfiguration;
   NumSplit ns;
   ns.heavy_bin = sp.heavy_bin;
+  ns.hi_bin = sp.hi_bin;
   ns.hcap = sp.hcap;
   ns.ntf = sp.ntf;
   ns.rr = sp.rr;
@@ -44,6 +46,25 @@ static cudaError_t warp_num(const LaunchCtx& c, const Csr& A, const Csr& B, cons
   const int grid = c.nsm * occ;
   k<<<grid, NUM_WARPS_CTA * 32, smem, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, ns, cur, nxt, c_rp, c_ci, c_v,
                                                   c.err);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+constexpr int NUM_BLOCK_WARPS = 16;
+
+template <typename T, int W>
+static cudaError_t block_num(const LaunchCtx& c, const Csr& A, const Csr& B, const T* av, const T* bv,
+                             const RowInfo& ri, int lo, int hi, const SplitInfo& sp, int32_t* cur, int32_t* nxt,
+                             const int32_t* c_rp, int32_t* c_ci, T* c_v) {
+  auto k = k_num_block<W, NUM_BLOCK_WARPS, T>;
+  const size_t smem = numblock_smem_bytes<W, NUM_BLOCK_WARPS, T>();
+  const int occ = kernel_blocks_per_sm(k, NUM_BLOCK_WARPS * 32, smem);
+  if (occ <= 0) return cudaErrorInvalidConfiguration;
+  unsigned* counter = &c.st->work[1];
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), c.stream);
+  if (e != cudaSuccess) return e;
+  k<<<c.nsm * occ, NUM_BLOCK_WARPS * 32, smem, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, sp.rr, sp.runs,
+                                                          sp.wf_shift, cur, nxt, c_rp, c_ci, c_v, counter, c.err);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -81,7 +102,8 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
     timer_mark(c, T_NUM_TINY, 1);
     if (e) return e;
   }
-  // every other row: the warp-owned dense window (symbolic warp and block
+  // every other row: the warp-owned dense window up to tu.num_lo_block,
+  // the block-wide window from there on (rows of the symbolic warp and block
   // paths both land here)
   int lo = NBINS, hi = 0;
   for (int p : {PATH_WARP, PATH_BLOCK})
@@ -89,6 +111,17 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
       lo = pb.lo[p] < lo ? pb.lo[p] : lo;
       hi = pb.hi[p] > hi ? pb.hi[p] : hi;
     }
+  const int blo = tu.num_lo_block > lo ? tu.num_lo_block : lo;
+  if (hi >= blo) {
+    timer_mark(c, T_NUM_BLOCK, 0);
+    if (tu.window_block == 16384)
+      e = block_num<T, 16384>(c, A, B, av, bv, ri, blo, hi, sp, cur, nxt, c_rp, c_ci, c_v);
+    else
+      e = block_num<T, 8192>(c, A, B, av, bv, ri, blo, hi, sp, cur, nxt, c_rp, c_ci, c_v);
+    timer_mark(c, T_NUM_BLOCK, 1);
+    if (e) return e;
+    hi = blo - 1;
+  }
   if (hi >= lo) {
     timer_mark(c, T_NUM_WARP, 0);
     switch (tu.window_warp) {

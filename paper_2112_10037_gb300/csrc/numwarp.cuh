@@ -32,7 +32,8 @@
 namespace sg {
 
 struct NumSplit {
-  int heavy_bin;          // rows in bins >= heavy_bin are split (within capacity)
+  int heavy_bin;          // rows in bins [heavy_bin, hi_bin] are split (within capacity)
+  int hi_bin;
   int hcap;               // capacity of the per-window count table (rows)
   int ntf;                // windows (of W columns) per row
   const int32_t* rr;      // B's run pointers (nrows(B) + 1)
@@ -209,9 +210,13 @@ k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
     bin_range(st, bin_lo, bin_hi, &b, &e);
     s_lb = b;
     s_le = e;
-    int hb, he;  // split rows: the leading rows of bins >= heavy_bin, within capacity
-    bin_range(st, sp.heavy_bin > bin_lo ? sp.heavy_bin : bin_lo, bin_hi, &hb, &he);
-    int nh = (sp.heavy_bin <= bin_hi && hb == b) ? he - hb : 0;
+    // split rows (bins [heavy_bin, hi_bin], the symbolic pass's numbering):
+    // only when they are the leading rows of this launch's range
+    int nh = 0, hb = 0, he = 0;
+    if (sp.heavy_bin < NBINS && sp.hi_bin >= sp.heavy_bin && sp.heavy_bin >= bin_lo && sp.hi_bin == bin_hi) {
+      bin_range(st, sp.heavy_bin, sp.hi_bin, &hb, &he);
+      if (hb == b) nh = he - hb;
+    }
     s_nh = nh < sp.hcap ? nh : sp.hcap;
   }
   if (block_skip(st)) return;

@@ -249,7 +249,7 @@ k_sym_window(Csr A, Csr B, RowInfo ri, const DevStats* st, int bin_lo, int bin_h
   constexpr int NTW = W / SYM_MIN_FINE + 2;  // fine tiles a window can touch
   constexpr size_t GB = sym_group_bytes<W, GW>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int s_lb, s_le, s_nh;
+  __shared__ int s_lb, s_le, s_nh, s_hs;
   const int warp = threadIdx.x >> 5, lane = lane_id();
   const int g = warp / GW, wig = warp % GW;
   unsigned char* gbase = smem_raw + (size_t)g * GB;
@@ -261,15 +261,16 @@ k_sym_window(Csr A, Csr B, RowInfo ri, const DevStats* st, int bin_lo, int bin_h
   for (int t = wig * 32 + lane; t < NTW; t += GW * 32) tcnt[t] = 0;
   if (threadIdx.x == 0) {
     bin_range(st, bin_lo, bin_hi, &s_lb, &s_le);
-    s_nh = split_rows(st, sp);
+    s_nh = split_rows(st, sp, &s_hs);
   }
   if (block_skip(st)) return;
-  const int lb = s_lb, le = s_le, nh = s_nh;
+  const int lb = s_lb, le = s_le, nh = s_nh, hs = s_hs;
   const int wf_shift = sp.wf_shift;
 
   for (long long idx = lb + (long long)blockIdx.x * NG + g; idx < le; idx += (long long)gridDim.x * NG) {
     const int r = ri.rows[idx];
-    const bool split = idx < nh;
+    const bool split = idx >= hs && idx < hs + nh;
+    const long long hrow = idx - hs;  // row of the per-window count table
     const long long i = ri.row_begin + r;
     const int a0 = A.rp[i], a1 = A.rp[i + 1], nA = a1 - a0;
     int base = ri.cmin[r] & ~31;
@@ -281,7 +282,7 @@ k_sym_window(Csr A, Csr B, RowInfo ri, const DevStats* st, int bin_lo, int bin_h
     long long rowcount = 0;
     bool first = true;
     if (split) {
-      for (int t = wig * 32 + lane; t < sp.ntf; t += GW * 32) sp.hcnt[(size_t)idx * sp.ntf + t] = 0;
+      for (int t = wig * 32 + lane; t < sp.ntf; t += GW * 32) sp.hcnt[(size_t)hrow * sp.ntf + t] = 0;
       group_sync<GW>(g);
     }
     while (true) {
@@ -376,7 +377,7 @@ k_sym_window(Csr A, Csr B, RowInfo ri, const DevStats* st, int bin_lo, int bin_h
         for (int t = wig * 32 + lane; t < ntw; t += GW * 32) {
           const int v = tcnt[t];
           if (v) {
-            atomicAdd(&sp.hcnt[(size_t)idx * sp.ntf + tile0 + t], v);
+            atomicAdd(&sp.hcnt[(size_t)hrow * sp.ntf + tile0 + t], v);
             tcnt[t] = 0;
           }
         }
