@@ -39,6 +39,10 @@ sys.path.insert(0, HERE)
 from paper_2112_10037_gb300 import gen  # noqa: E402
 
 L2_BYTES = 129 * 1024 * 1024
+# default row classes of the library (register sort <= 128 products; numeric
+# warp window up to 32768 products, bins rounded to powers of two; block
+# window above)
+NUM_BLOCK_MIN = 32768
 PEAKS_FILE = os.path.join(HERE, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -294,7 +298,8 @@ def kernel_bytes(A, B, prod_rows, c_rp, kernel, row_begin):
     # register sort up to 128 products; every larger row runs in the warp
     # window kernel (numeric) / the bitmap kernels (symbolic warp <= 8192 < block)
     if kernel.startswith("num"):
-        lo, hi = {"tiny": (1, 128), "warp": (129, 1 << 62)}.get(path, (0, -1))
+        lo, hi = {"tiny": (1, 128), "warp": (129, NUM_BLOCK_MIN), "block": (NUM_BLOCK_MIN + 1, 1 << 62)}.get(
+            path, (0, -1))
     else:
         lo, hi = {"tiny": (1, 128), "warp": (129, 8192), "block": (8193, 1 << 62)}.get(path, (0, -1))
     rows = np.flatnonzero((P >= lo) & (P <= hi))
@@ -321,7 +326,9 @@ def kernel_products(prod_rows, kernel):
     P = np.asarray(prod_rows, np.int64)
     if kernel == "num_tiny":
         return int(P[(P >= 1) & (P <= 128)].sum())
-    return int(P[P > 128].sum())
+    if kernel == "num_warp":
+        return int(P[(P > 128) & (P <= NUM_BLOCK_MIN)].sum())
+    return int(P[P > NUM_BLOCK_MIN].sum())
 
 
 def fp64_peak_gflops(torch, dev):

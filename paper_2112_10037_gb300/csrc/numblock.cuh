@@ -19,9 +19,61 @@
 
 namespace sg {
 
+// Long segments (at least NB_LONG entries) are cut into pieces of
+// NB_PIECE products and queued in shared memory; after the warps have read
+// their nonzeros' segments, all warps take pieces from the queue, so one hub
+// row of B no longer keeps a single warp busy while the others wait.
+constexpr int NB_LONG = 128;
+constexpr int NB_PIECE = 256;
+constexpr int NB_QCAP = 512;
+
+template <typename T>
+struct NbPiece {
+  int s;    // first position in B
+  int len;  // products in this piece
+  T a;      // A(i,k)
+};
+
 template <int W, int NW, typename T>
 __host__ __device__ constexpr size_t numblock_smem_bytes() {
-  return (size_t)W * sizeof(T) + (size_t)(W / 32) * 4 + (size_t)NW * 8 + 16;
+  return (size_t)W * sizeof(T) + (size_t)(W / 32) * 4 + (size_t)NW * 8 + 16 +
+         (size_t)NB_QCAP * sizeof(NbPiece<T>) + 16;
+}
+
+// Products of one segment piece by the whole warp (distinct columns inside
+// the piece; other warps may hit the same columns, hence atomics).
+template <int W, typename T>
+__device__ __forceinline__ void nb_piece(const Csr& B, const T* __restrict__ bv, int s, int len, T a, int base,
+                                         T* acc, uint32_t* bits, uint32_t* err) {
+  const int lane = lane_id();
+  int t = lane;
+  for (; t + 96 < len; t += 128) {
+    const int q = s + t;
+    const int j0 = B.ci[q] - base, j1 = B.ci[q + 32] - base, j2 = B.ci[q + 64] - base, j3 = B.ci[q + 96] - base;
+    const T b0 = bv[q], b1 = bv[q + 32], b2 = bv[q + 64], b3 = bv[q + 96];
+    if (((unsigned)j0 | (unsigned)j1 | (unsigned)j2 | (unsigned)j3) < (unsigned)W) {
+      atomicOr(&bits[j0 >> 5], 1u << (j0 & 31));
+      atomicAdd(&acc[j0], a * b0);
+      atomicOr(&bits[j1 >> 5], 1u << (j1 & 31));
+      atomicAdd(&acc[j1], a * b1);
+      atomicOr(&bits[j2 >> 5], 1u << (j2 & 31));
+      atomicAdd(&acc[j2], a * b2);
+      atomicOr(&bits[j3 >> 5], 1u << (j3 & 31));
+      atomicAdd(&acc[j3], a * b3);
+    } else {
+      atomicOr(err, EB_UNSORTED);
+    }
+  }
+  for (; t < len; t += 32) {
+    const int q = s + t;
+    const int jj = B.ci[q] - base;
+    if ((unsigned)jj < (unsigned)W) {
+      atomicOr(&bits[jj >> 5], 1u << (jj & 31));
+      atomicAdd(&acc[jj], a * bv[q]);
+    } else {
+      atomicOr(err, EB_UNSORTED);
+    }
+  }
 }
 
 template <int W, int NW, typename T>
@@ -37,11 +89,17 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
   uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw + (size_t)W * sizeof(T));
   int* wcnt = reinterpret_cast<int*>(bits + NWORDS);
   int* wnext = wcnt + NW;
-  __shared__ int s_lb, s_le, s_item;
+  NbPiece<T>* queue = reinterpret_cast<NbPiece<T>*>(
+      smem_raw + (((size_t)W * sizeof(T) + (size_t)NWORDS * 4 + (size_t)NW * 8 + 16 + 15) & ~(size_t)15));
+  __shared__ int s_lb, s_le, s_item, s_qn, s_qtake;
   const int warp = threadIdx.x >> 5, lane = lane_id();
   for (int t = threadIdx.x; t < W; t += NW * 32) acc[t] = T(0);
   for (int t = threadIdx.x; t < NWORDS; t += NW * 32) bits[t] = 0u;
-  if (threadIdx.x == 0) bin_range(st, bin_lo, bin_hi, &s_lb, &s_le);
+  if (threadIdx.x == 0) {
+    bin_range(st, bin_lo, bin_hi, &s_lb, &s_le);
+    s_qn = 0;
+    s_qtake = 0;
+  }
   if (block_skip(st)) return;
   const int lb = s_lb, le = s_le;
   const int wshift = 31 - __clz(W);      // block window width
@@ -108,42 +166,40 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
           }
           mn = min(mn, wid);
         }
-        // products: long segments by the whole warp, short ones flattened
-        unsigned lm = __ballot_sync(FULL, len >= 32);
+        // very long segments: queue their pieces for all warps (warp-aggregated
+        // reservation); if the queue is full the warp keeps the segment
+        bool keep = len >= 32;
+        if (len >= NB_LONG) {
+          const int np = (len + NB_PIECE - 1) / NB_PIECE;
+          const int at = atomicAdd(&s_qn, np);  // reserve np slots
+          if (at + np <= NB_QCAP) {
+            for (int p = 0; p < np; ++p) {
+              NbPiece<T> pc;
+              pc.s = s + p * NB_PIECE;
+              pc.len = min(NB_PIECE, len - p * NB_PIECE);
+              pc.a = a;
+              queue[at + p] = pc;
+            }
+            keep = false;
+          } else {
+            // queue full: the slots reserved below the capacity stay empty
+            for (int p = at; p < NB_QCAP && p < at + np; ++p) {
+              NbPiece<T> pc;
+              pc.s = 0;
+              pc.len = 0;
+              pc.a = T(0);
+              queue[p] = pc;
+            }
+          }
+        }
+        // remaining long segments by the whole warp, short ones flattened
+        unsigned lm = __ballot_sync(FULL, keep);
         while (lm) {
           const int L = __ffs(lm) - 1;
           lm &= lm - 1;
           const int ls = __shfl_sync(FULL, s, L), ln = __shfl_sync(FULL, len, L);
           const T la = __shfl_sync(FULL, a, L);
-          int t = lane;
-          for (; t + 96 < ln; t += 128) {
-            const int q = ls + t;
-            const int j0 = B.ci[q] - base, j1 = B.ci[q + 32] - base, j2 = B.ci[q + 64] - base,
-                      j3 = B.ci[q + 96] - base;
-            const T b0 = bv[q], b1 = bv[q + 32], b2 = bv[q + 64], b3 = bv[q + 96];
-            if (((unsigned)j0 | (unsigned)j1 | (unsigned)j2 | (unsigned)j3) < (unsigned)W) {
-              atomicOr(&bits[j0 >> 5], 1u << (j0 & 31));
-              atomicAdd(&acc[j0], la * b0);
-              atomicOr(&bits[j1 >> 5], 1u << (j1 & 31));
-              atomicAdd(&acc[j1], la * b1);
-              atomicOr(&bits[j2 >> 5], 1u << (j2 & 31));
-              atomicAdd(&acc[j2], la * b2);
-              atomicOr(&bits[j3 >> 5], 1u << (j3 & 31));
-              atomicAdd(&acc[j3], la * b3);
-            } else {
-              atomicOr(err, EB_UNSORTED);
-            }
-          }
-          for (; t < ln; t += 32) {
-            const int q = ls + t;
-            const int jj = B.ci[q] - base;
-            if ((unsigned)jj < (unsigned)W) {
-              atomicOr(&bits[jj >> 5], 1u << (jj & 31));
-              atomicAdd(&acc[jj], la * bv[q]);
-            } else {
-              atomicOr(err, EB_UNSORTED);
-            }
-          }
+          nb_piece<W, T>(B, bv, ls, ln, la, base, acc, bits, err);
         }
         const int sl = len < 32 ? len : 0;
         const int incl = warp_incl_scan(sl);
@@ -167,6 +223,18 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
         }
       }
       mn = warp_min(mn);
+      __syncthreads();  // the queue is complete
+      {
+        const int qn = min(s_qn, NB_QCAP);
+        while (true) {
+          int pi = 0;
+          if (lane == 0) pi = atomicAdd(&s_qtake, 1);
+          pi = __shfl_sync(FULL, pi, 0);
+          if (pi >= qn) break;
+          const NbPiece<T> pc = queue[pi];
+          nb_piece<W, T>(B, bv, pc.s, pc.len, pc.a, base, acc, bits, err);
+        }
+      }
       // emission: each warp takes NWORDS / NW consecutive words of the bitmap
       const int ncols = min(W, cmx - base + 1);
       const int nwd = (ncols + 31) >> 5;
@@ -179,6 +247,10 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
       if (lane == 0) {
         wcnt[warp] = cnt;
         wnext[warp] = mn;
+      }
+      if (threadIdx.x == 0) {  // queue drained by everyone (all past the barrier above)
+        s_qn = 0;
+        s_qtake = 0;
       }
       __syncthreads();
       int before = 0, total = 0, nb = INT_MAX;

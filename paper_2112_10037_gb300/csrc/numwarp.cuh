@@ -315,13 +315,20 @@ k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
         for (int q = 0; q < NW_SLOTS; ++q) {
           if (q < nslots) {
             const bool act = wid[q] == w;
+            // issue the loads of the next run before this window's products,
+            // so their latency overlaps the accumulation
+            int2 nx = make_int2(wid[q], s0[q]);
+            int nend = s1[q];
+            if (act) {
+              nx = sp.runs[rj[q] + 1];
+              if (nx.x != INT_MAX) nend = sp.runs[rj[q] + 2].y;
+            }
             win.segments(B, bv, s0[q], act ? s1[q] - s0[q] : 0, a[q], base);
             if (act) {  // advance to the next run of this B row
               ++rj[q];
-              const int2 nx = sp.runs[rj[q]];
               wid[q] = nx.x;
               s0[q] = nx.y;
-              if (nx.x != INT_MAX) s1[q] = sp.runs[rj[q] + 1].y;
+              s1[q] = nend;
             }
             mn = min(mn, wid[q]);
           }

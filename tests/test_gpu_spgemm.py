@@ -273,3 +273,27 @@ def test_register_sort_multi_slot(api, oracle_mod, P):
     R = oracle_mod.spgemm(A, B)
     assert_structure_equal(C, R)
     assert_values_exact(C.vals, R.vals)
+
+
+@pytest.mark.parametrize("num_block_min", [256, 4096])
+def test_block_window_queue_overflow_and_long_segments(api, oracle_mod, num_block_min):
+    """Rows with thousands of long B segments per window (queue overflow) and
+    hub columns hit by every segment, through the block-window kernel."""
+    rng = np.random.default_rng(17)
+    counts = rng.integers(50, 800, size=40)
+    counts[:3] = [2000, 1500, 1200]
+    A = gen.random_rows(40, 3000, counts, rng, values="int")
+    cB = rng.integers(100, 400, size=3000)
+    B = gen.random_rows(3000, 9000, cB, rng, values="int")
+    # every row of B also hits the first 40 columns (hub columns)
+    rows = []
+    rp = B.row_ptr.astype(np.int64)
+    for k in range(B.nrows):
+        rows.append(np.unique(np.concatenate([np.arange(40), B.col_idx[rp[k]:rp[k + 1]]])))
+    ci = np.concatenate(rows).astype(np.int32)
+    nrp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    B = gen.CSR(B.nrows, B.ncols, nrp, ci, rng.integers(-3, 4, len(ci)).astype(np.float64))
+    C, _ = run(api, A, B, num_block_min=num_block_min)
+    R = oracle_mod.spgemm(A, B)
+    assert_structure_equal(C, R)
+    assert_values_exact(C.vals, R.vals)
