@@ -84,7 +84,7 @@ typedef struct spgemm_opts {
                           hash accumulator (0: library default; -1: never) */
   int32_t window_warp; /* columns of the numeric dense window (one per warp):
                           1024, 2048 or 4096 (0: default 1024) */
-  int32_t window_block;/* columns of the numeric block window: 8192 or 16384 (0: 8192) */
+  int32_t window_block;/* columns of the numeric block window: 4096, 8192 or 16384 (0: 8192) */
   int32_t split_min;   /* rows with more products than this are split into column
                           tiles of window_warp columns, processed independently
                           (0: default 131072; -1: never split); used only for rows
@@ -94,7 +94,8 @@ typedef struct spgemm_opts {
   int32_t num_block_min;/* rows with more products than this run the numeric pass
                           with a block-wide window (0: default 32768; -1: never, then
                           heavy rows are split as split_min says) */
-  int32_t reserved[4];
+  int32_t block_warps; /* warps sharing a numeric block window: 8 or 16 (0: 16) */
+  int32_t reserved[3];
 } spgemm_opts;
 
 typedef struct spgemm_plan spgemm_plan;

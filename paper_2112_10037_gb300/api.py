@@ -62,7 +62,8 @@ def _stream_handle(stream=None) -> int:
 
 
 def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1, warp_max=0,
-              window_warp=0, window_block=0, split_min=0, backward=False, num_block_min=0) -> nat.spgemm_opts:
+              window_warp=0, window_block=0, split_min=0, backward=False, num_block_min=0,
+              block_warps=0) -> nat.spgemm_opts:
     o = nat.spgemm_opts_default()
     o.dtype = _DT[dtype]
     o.validate = 1 if validate else 0
@@ -75,6 +76,7 @@ def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1
     o.split_min = int(split_min)
     o.backward = 1 if backward else 0
     o.num_block_min = int(num_block_min)
+    o.block_warps = int(block_warps)
     return o
 
 

@@ -170,7 +170,8 @@ void choose_paths(const spgemm_opts& o, sg::PathBins* pb, sg::Tuning* tu) {
   const int last = sg::NBINS - 1;
   tu->warp_max = o.warp_max > 0 ? o.warp_max : 8192;
   tu->window_warp = numeric_window(o);
-  tu->window_block = o.window_block == 16384 ? 16384 : 8192;
+  tu->window_block = (o.window_block == 16384 || o.window_block == 4096) ? o.window_block : 8192;
+  tu->block_warps = o.block_warps == 8 ? 8 : 16;
   tu->hash_max = 0;
   tu->num_lo_block = numeric_block_bin(o);
   constexpr int TINY_HI = 8;  // register sort up to 128 products
@@ -251,6 +252,7 @@ void spgemm_opts_default(spgemm_opts* o) {
   o->split_min = 0;
   o->backward = 0;
   o->num_block_min = 0;
+  o->block_warps = 0;
 }
 
 const char* spgemm_status_string(spgemm_status s) {

@@ -85,6 +85,7 @@ struct Tuning {
   int hash_max;        // largest P of the hash path (0: path disabled)
   int warp_max;        // largest P of the symbolic warp path
   int num_lo_block;    // numeric bins >= this use the block kernel (NBINS: never)
+  int block_warps;     // warps per numeric block window
 };
 
 // Window-run list of B: the numeric pass uses windows of 2^wf_shift columns

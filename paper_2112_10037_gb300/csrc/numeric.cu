@@ -50,9 +50,7 @@ static cudaError_t warp_num(const LaunchCtx& c, const Csr& A, const Csr& B, cons
   return cudaGetLastError();
 }
 
-constexpr int NUM_BLOCK_WARPS = 16;
-
-template <typename T, int W>
+template <typename T, int W, int NUM_BLOCK_WARPS>
 static cudaError_t block_num(const LaunchCtx& c, const Csr& A, const Csr& B, const T* av, const T* bv,
                              const RowInfo& ri, int lo, int hi, const SplitInfo& sp, int32_t* cur, int32_t* nxt,
                              const int32_t* c_rp, int32_t* c_ci, T* c_v) {
@@ -114,10 +112,17 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
   const int blo = tu.num_lo_block > lo ? tu.num_lo_block : lo;
   if (hi >= blo) {
     timer_mark(c, T_NUM_BLOCK, 0);
-    if (tu.window_block == 16384)
-      e = block_num<T, 16384>(c, A, B, av, bv, ri, blo, hi, sp, cur, nxt, c_rp, c_ci, c_v);
-    else
-      e = block_num<T, 8192>(c, A, B, av, bv, ri, blo, hi, sp, cur, nxt, c_rp, c_ci, c_v);
+#define SG_BLOCK_NUM(WW, NWW) e = block_num<T, WW, NWW>(c, A, B, av, bv, ri, blo, hi, sp, cur, nxt, c_rp, c_ci, c_v)
+    if (tu.block_warps == 8) {
+      if (tu.window_block == 16384) SG_BLOCK_NUM(16384, 8);
+      else if (tu.window_block == 4096) SG_BLOCK_NUM(4096, 8);
+      else SG_BLOCK_NUM(8192, 8);
+    } else {
+      if (tu.window_block == 16384) SG_BLOCK_NUM(16384, 16);
+      else if (tu.window_block == 4096) SG_BLOCK_NUM(4096, 16);
+      else SG_BLOCK_NUM(8192, 16);
+    }
+#undef SG_BLOCK_NUM
     timer_mark(c, T_NUM_BLOCK, 1);
     if (e) return e;
     hi = blo - 1;
