@@ -84,7 +84,10 @@ typedef struct spgemm_opts {
                           hash accumulator (0: library default; -1: never) */
   int32_t window_warp; /* columns of the numeric dense window (one per warp):
                           1024, 2048 or 4096 (0: default 1024) */
-  int32_t window_block;/* columns of the numeric block window: 4096, 8192 or 16384 (0: 8192) */
+  int32_t window_block;/* columns of the numeric block window, with block_warps one of
+                          the pairs (2048, 4), (2048, 8), (4096, 4), (4096, 8),
+                          (4096, 16), (8192, 8), (8192, 16), (16384, 16); 0 or any
+                          other pair: (8192, 8) */
   int32_t split_min;   /* rows with more products than this are split into column
                           tiles of window_warp columns, processed independently
                           (0: default 131072; -1: never split); used only for rows
@@ -94,7 +97,7 @@ typedef struct spgemm_opts {
   int32_t num_block_min;/* rows with more products than this run the numeric pass
                           with a block-wide window (0: default 32768; -1: never, then
                           heavy rows are split as split_min says) */
-  int32_t block_warps; /* warps sharing a numeric block window: 8 or 16 (0: 16) */
+  int32_t block_warps; /* warps sharing a numeric block window (see window_block) */
   int32_t reserved[3];
 } spgemm_opts;
 

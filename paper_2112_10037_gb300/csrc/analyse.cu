@@ -126,64 +126,89 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const long long* __restrict
 
 static int grid_for_warps(long long nwarps, int warps_per_block, int nsm);
 
-// Window-run list of B (see SplitInfo): pass 1 counts the runs of each row
-// (plus its sentinel), an exclusive scan turns counts into run pointers,
-// pass 2 writes (window id, first position) of every run.  One warp per row;
-// a run starts where the window id differs from the previous entry's.
-__global__ void __launch_bounds__(256) k_runs_count(Csr B, int wshift, int32_t* __restrict__ rr, const DevStats* st) {
+// Window-run lists of B (see SplitInfo), at two window widths (shifts s1
+// and s2) from one read of B: pass 1 counts the runs of each row (plus its
+// sentinel), an exclusive scan turns counts into run pointers, pass 2 writes
+// (window id, first position) of every run.  One warp per row; a run starts
+// where the window id differs from the previous entry's.  A null second list
+// is skipped.
+__global__ void __launch_bounds__(256) k_runs_count(Csr B, int s1, int32_t* __restrict__ rr1, int s2,
+                                                    int32_t* __restrict__ rr2, const DevStats* st) {
   if (block_skip(st)) return;
   const int lane = lane_id();
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
   for (long long k = w; k < B.nrows; k += nw) {
     const int rs = B.rp[k], re = B.rp[k + 1];
-    int n = 0;
-    for (int idx = rs + lane; idx < re; idx += 32) {
-      const int wid = B.ci[idx] >> wshift;
-      const bool start = idx == rs || (B.ci[idx - 1] >> wshift) != wid;
-      n += __popc(__ballot_sync(__activemask(), start));
+    int n1 = 0, n2 = 0;
+    for (int base = rs; base < re; base += 32) {
+      const int idx = base + lane;
+      bool b1 = false, b2 = false;
+      if (idx < re) {
+        const int c = B.ci[idx], pc = idx == rs ? -1 : B.ci[idx - 1];
+        b1 = idx == rs || (pc >> s1) != (c >> s1);
+        b2 = idx == rs || (pc >> s2) != (c >> s2);
+      }
+      n1 += __popc(__ballot_sync(FULL, b1));
+      n2 += __popc(__ballot_sync(FULL, b2));
     }
-    n = __shfl_sync(FULL, n, 0);
-    if (lane == 0) rr[k] = n + 1;
+    if (lane == 0) {
+      rr1[k] = n1 + 1;
+      if (rr2) rr2[k] = n2 + 1;
+    }
   }
 }
 
-__global__ void __launch_bounds__(256) k_runs_fill(Csr B, int wshift, const int32_t* __restrict__ rr,
-                                                   int2* __restrict__ runs, const DevStats* st) {
-  if (block_skip(st)) return;
+__device__ __forceinline__ void runs_fill_row(const Csr& B, int k, int shift, const int32_t* __restrict__ rr,
+                                              int2* __restrict__ runs) {
   const int lane = lane_id();
+  const int rs = B.rp[k], re = B.rp[k + 1];
+  int pos = rr[k];
+  for (int base = rs; base < re; base += 32) {
+    const int idx = base + lane;
+    bool start = false;
+    int wid = 0;
+    if (idx < re) {
+      wid = B.ci[idx] >> shift;
+      start = idx == rs || (B.ci[idx - 1] >> shift) != wid;
+    }
+    const unsigned m = __ballot_sync(FULL, start);
+    if (start) runs[pos + __popc(m & lanemask_lt())] = make_int2(wid, idx);
+    pos += __popc(m);
+  }
+  if (lane == 0) runs[rr[k + 1] - 1] = make_int2(INT_MAX, re);
+}
+
+__global__ void __launch_bounds__(256) k_runs_fill(Csr B, int s1, const int32_t* __restrict__ rr1,
+                                                   int2* __restrict__ runs1, int s2, const int32_t* __restrict__ rr2,
+                                                   int2* __restrict__ runs2, const DevStats* st) {
+  if (block_skip(st)) return;
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
   for (long long k = w; k < B.nrows; k += nw) {
-    const int rs = B.rp[k], re = B.rp[k + 1];
-    int pos = rr[k];
-    for (int base = rs; base < re; base += 32) {
-      const int idx = base + lane;
-      bool start = false;
-      int wid = 0;
-      if (idx < re) {
-        wid = B.ci[idx] >> wshift;
-        start = idx == rs || (B.ci[idx - 1] >> wshift) != wid;
-      }
-      const unsigned m = __ballot_sync(FULL, start);
-      if (start) runs[pos + __popc(m & lanemask_lt())] = make_int2(wid, idx);
-      pos += __popc(m);
-    }
-    if (lane == 0) runs[rr[k + 1] - 1] = make_int2(INT_MAX, re);
+    runs_fill_row(B, (int)k, s1, rr1, runs1);
+    if (runs2) runs_fill_row(B, (int)k, s2, rr2, runs2);
   }
 }
 
 cudaError_t launch_runs(const LaunchCtx& c, const Csr& B, const SplitInfo& sp, long long* partials) {
   if (!sp.rr || !sp.runs) return cudaSuccess;
-  if (B.nrows <= 0) return cudaMemsetAsync(sp.rr, 0, sizeof(int32_t), c.stream);
+  const bool two = sp.rrb && sp.runsb;
+  if (B.nrows <= 0) {
+    cudaError_t e = cudaMemsetAsync(sp.rr, 0, sizeof(int32_t), c.stream);
+    if (e == cudaSuccess && two) e = cudaMemsetAsync(sp.rrb, 0, sizeof(int32_t), c.stream);
+    return e;
+  }
   const int grid = grid_for_warps(B.nrows, 8, c.nsm);
-  k_runs_count<<<grid, 256, 0, c.stream>>>(B, sp.wf_shift, sp.rr, c.st);
+  k_runs_count<<<grid, 256, 0, c.stream>>>(B, sp.wf_shift, sp.rr, sp.wb_shift, two ? sp.rrb : nullptr, c.st);
   count_launch(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = launch_scan(c, sp.rr, B.nrows, partials, &c.st->nruns);
+  if (e == cudaSuccess && two) e = launch_scan(c, sp.rrb, B.nrows, partials, &c.st->nruns_b);
   if (e != cudaSuccess) return e;
-  k_runs_fill<<<grid, 256, 0, c.stream>>>(B, sp.wf_shift, sp.rr, sp.runs, c.st);
+  k_runs_fill<<<grid, 256, 0, c.stream>>>(B, sp.wf_shift, sp.rr, sp.runs, sp.wb_shift, two ? sp.rrb : nullptr,
+                                          two ? sp.runsb : nullptr, c.st);
   count_launch(c);
   return cudaGetLastError();
 }

@@ -55,7 +55,7 @@ constexpr size_t ALIGN = 256;
 inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 
 struct Layout {
-  size_t st, prod, cmin, cmax, rows, cursor, nxt, scan, rr, runs, runs_part, hcnt;
+  size_t st, prod, cmin, cmax, rows, cursor, nxt, scan, rr, runs, runs_part, hcnt, rrb, runsb;
   size_t at_rp, at_ci, at_src, at_fill, at_tmp, at_part;  // opts.backward only
   size_t total;
 };
@@ -130,9 +130,14 @@ Layout layout_for(const spgemm_opts& o, long long mloc, long long nnz_a, long lo
   L.nxt = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
   L.scan = off; off = align_up(off + sizeof(long long) * sg::scan_partials_count(mloc));
   L.rr = off; off = align_up(off + sizeof(int32_t) * (size_t)(nrows_b + 1));
-  L.runs = off; off = align_up(off + sizeof(int2) * (size_t)(nnz_b + nrows_b));
+  L.runs = off; off = align_up(off + sizeof(int2) * (size_t)(nnz_b + nrows_b + sg::RUNS_PAD));
   L.runs_part = off; off = align_up(off + sizeof(long long) * sg::scan_partials_count(nrows_b));
   L.hcnt = off; off = align_up(off + sizeof(int32_t) * nh);
+  L.rrb = L.runsb = 0;
+  if (numeric_block_bin(o) < sg::NBINS) {  // run list at the block window's width
+    L.rrb = off; off = align_up(off + sizeof(int32_t) * (size_t)(nrows_b + 1));
+    L.runsb = off; off = align_up(off + sizeof(int2) * (size_t)(nnz_b + nrows_b + sg::RUNS_PAD));
+  }
   if (o.backward) {
     L.at_rp = off; off = align_up(off + sizeof(int32_t) * (size_t)(nrows_b + 1));
     L.at_ci = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
@@ -165,13 +170,28 @@ spgemm_status check_csr(const spgemm_csr* M) {
   return SPGEMM_OK;
 }
 
+// Window columns and warps of the numeric block kernel: one of the compiled
+// pairs, the default where the options name none or an unsupported one.
+static void block_geometry(const spgemm_opts& o, int* w, int* nw) {
+  static const int pairs[][2] = {{2048, 4}, {2048, 8}, {4096, 4}, {4096, 8}, {4096, 16}, {8192, 8}, {8192, 16},
+                                 {16384, 16}};
+  const int dw = 8192, dn = 8;  // default geometry
+  const int ww = o.window_block > 0 ? o.window_block : dw, nn = o.block_warps > 0 ? o.block_warps : dn;
+  *w = dw;
+  *nw = dn;
+  for (const auto& p : pairs)
+    if (p[0] == ww && p[1] == nn) {
+      *w = ww;
+      *nw = nn;
+    }
+}
+
 // Bin ranges of the paths from the options (see sg::bin_of for the bins).
 void choose_paths(const spgemm_opts& o, sg::PathBins* pb, sg::Tuning* tu) {
   const int last = sg::NBINS - 1;
   tu->warp_max = o.warp_max > 0 ? o.warp_max : 8192;
   tu->window_warp = numeric_window(o);
-  tu->window_block = (o.window_block == 16384 || o.window_block == 4096) ? o.window_block : 8192;
-  tu->block_warps = o.block_warps == 8 ? 8 : 16;
+  block_geometry(o, &tu->window_block, &tu->block_warps);
   tu->hash_max = 0;
   tu->num_lo_block = numeric_block_bin(o);
   constexpr int TINY_HI = 8;  // register sort up to 128 products
@@ -333,6 +353,10 @@ spgemm_status spgemm_analyse(const spgemm_csr* A, const spgemm_csr* B, const spg
     p->sp.rr = (int32_t*)(p->ws + L.rr);
     p->sp.runs = (int2*)(p->ws + L.runs);
     p->sp.hcnt = nh ? (int32_t*)(p->ws + L.hcnt) : nullptr;
+    p->sp.wb_shift = 0;
+    while ((1 << p->sp.wb_shift) < p->tu.window_block) ++p->sp.wb_shift;
+    p->sp.rrb = L.rrb ? (int32_t*)(p->ws + L.rrb) : nullptr;
+    p->sp.runsb = L.runsb ? (int2*)(p->ws + L.runsb) : nullptr;
     p->runs_part = (long long*)(p->ws + L.runs_part);
   }
 

@@ -43,6 +43,7 @@ struct DevStats {
   unsigned long long max_products;
   long long nnz_c;
   long long nruns;   // entries of B's window-run list
+  long long nruns_b;  // entries of its block-window-granular copy
   long long scratch_total;  // total of the transpose's prefix sum
   uint32_t err;
   uint32_t pad;
@@ -107,7 +108,17 @@ struct SplitInfo {
   int32_t* rr;        // nrows(B) + 1 run pointers
   int2* runs;         // (window id, start) per run, sentinel-terminated rows
   int32_t* hcnt;      // hcap x ntf output counts
+  // the same run list at the numeric block window's granularity (log2 of its
+  // width in wb_shift); null when the plan has no block window
+  int wb_shift;
+  int32_t* rrb;
+  int2* runsb;
 };
+
+// Entries allocated past the last run, so that a kernel may read the few
+// runs after a row's current one in parallel without a bounds check (it
+// stops at the row's sentinel; what lies beyond is never used).
+constexpr int RUNS_PAD = 4;
 
 // ---------------------------------------------------------------- warp utils
 constexpr unsigned FULL = 0xffffffffu;
@@ -148,6 +159,14 @@ __device__ __forceinline__ int warp_max(int v) {
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) v = max(v, __shfl_xor_sync(FULL, v, d));
   return v;
+}
+
+// acc += v on a shared-memory word, result unused (a reduction, not a fetch).
+__device__ __forceinline__ void red_add_shared(double* p, double v) {
+  asm volatile("red.shared.add.f64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "d"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_shared(float* p, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v) : "memory");
 }
 
 // Index of the first lane whose inclusive prefix `incl` exceeds p (incl is

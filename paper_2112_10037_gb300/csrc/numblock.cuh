@@ -3,12 +3,21 @@
 // Row i of C is the sum over A(i,k) of A(i,k) * B(k,:) (Sec. 2.2).  One block
 // of NW warps owns one row at a time and a window of W consecutive columns
 // (a multiple of the run width of B's window-run list, aligned to W): a
-// dense value array and a presence bitmap in shared memory.  The row's
-// nonzeros are dealt to the warps in chunks; for each window, a nonzero's
-// segment of B(k,:) is the union of its consecutive runs whose window ids
-// fall in the block window, so it is found by reading a few run entries, with
-// no search.  Products from all warps land in the shared window, so they are
-// added with shared-memory atomics (the hardware resolves equal addresses).
+// dense value array and a presence bitmap in shared memory.  For each
+// window, a nonzero's segment of B(k,:) is the union of its consecutive runs
+// whose window ids fall in the block window, so it is found by reading a few
+// run entries, with no search.
+//
+// The segments of a window are first collected into a list in shared memory
+// together with their offsets in the window's product stream (the
+// concatenation of all segments).  The warps then take the stream in batches
+// of 32 consecutive products, whatever segments they come from: every lane of
+// every batch carries one product, so the FP64 pipe -- which spends the same
+// time on a warp instruction whatever the number of active lanes -- is used
+// at full width, and a long segment spreads over all warps by itself.
+// Products from all warps land in the shared window, so they are added with
+// shared-memory atomics (the hardware resolves equal addresses).
+//
 // The window is emitted in column order: every warp popcounts its share of
 // the bitmap, a block prefix places the shares, lanes write their bits.
 // Compared with one warp per row, a block window is W/1024 times wider, so a
@@ -19,91 +28,229 @@
 
 namespace sg {
 
-// Long segments (at least NB_LONG entries) are cut into pieces of
-// NB_PIECE products and queued in shared memory; after the warps have read
-// their nonzeros' segments, all warps take pieces from the queue, so one hub
-// row of B no longer keeps a single warp busy while the others wait.
-constexpr int NB_LONG = 128;
-constexpr int NB_PIECE = 256;
-constexpr int NB_QCAP = 512;
-
-template <typename T>
-struct NbPiece {
-  int s;    // first position in B
-  int len;  // products in this piece
-  T a;      // A(i,k)
-};
+// Nonzeros of A whose segments are collected per round: a nonzero has at most
+// one segment in a block window, so the list never holds more entries.  Small
+// blocks get a short list, so that more of them fit on an SM.
+template <int NW>
+__host__ __device__ constexpr int nb_segcap() {
+  return NW >= 16 ? 1024 : 64 * NW;
+}
 
 template <int W, int NW, typename T>
 __host__ __device__ constexpr size_t numblock_smem_bytes() {
-  return (size_t)W * sizeof(T) + (size_t)(W / 32) * 4 + (size_t)NW * 8 + 16 +
-         (size_t)NB_QCAP * sizeof(NbPiece<T>) + 16;
+  return (size_t)W * sizeof(T)                 // window values
+         + (size_t)nb_segcap<NW>() * sizeof(T)  // segment multipliers A(i,k)
+         + (size_t)(W / 32) * 4                // presence bitmap
+         + (size_t)nb_segcap<NW>() * 8         // segment stream offsets and starts in B
+         + (size_t)NW * 8;                     // per-warp counts and next windows
 }
 
-// Products of one segment piece by the whole warp (distinct columns inside
-// the piece; other warps may hit the same columns, hence atomics).
-template <int W, typename T>
-__device__ __forceinline__ void nb_piece(const Csr& B, const T* __restrict__ bv, int s, int len, T a, int base,
-                                         T* acc, uint32_t* bits, uint32_t* err) {
+// Last segment k in [0, nseg) whose stream offset is <= p (offsets strictly
+// increase, off[0] == 0 <= p, nseg <= 1024): two 32-way steps.
+__device__ __forceinline__ int nb_find_segment(const int* off, int nseg, int p) {
   const int lane = lane_id();
-  int t = lane;
-  for (; t + 96 < len; t += 128) {
-    const int q = s + t;
-    const int j0 = B.ci[q] - base, j1 = B.ci[q + 32] - base, j2 = B.ci[q + 64] - base, j3 = B.ci[q + 96] - base;
-    const T b0 = bv[q], b1 = bv[q + 32], b2 = bv[q + 64], b3 = bv[q + 96];
-    if (((unsigned)j0 | (unsigned)j1 | (unsigned)j2 | (unsigned)j3) < (unsigned)W) {
-      atomicOr(&bits[j0 >> 5], 1u << (j0 & 31));
-      atomicAdd(&acc[j0], a * b0);
-      atomicOr(&bits[j1 >> 5], 1u << (j1 & 31));
-      atomicAdd(&acc[j1], a * b1);
-      atomicOr(&bits[j2 >> 5], 1u << (j2 & 31));
-      atomicAdd(&acc[j2], a * b2);
-      atomicOr(&bits[j3 >> 5], 1u << (j3 & 31));
-      atomicAdd(&acc[j3], a * b3);
-    } else {
-      atomicOr(err, EB_UNSORTED);
-    }
+  int idx = lane * 32;
+  unsigned b = __ballot_sync(FULL, idx < nseg && off[idx] <= p);
+  const int f1 = (31 - __clz(b)) * 32;
+  idx = f1 + lane;
+  b = __ballot_sync(FULL, idx < nseg && off[idx] <= p);
+  return f1 + (31 - __clz(b));
+}
+
+// Loads of one step of U batches of 32 products from pb on: column, B value
+// and multiplier of every lane's product.  f is the segment of product pb on
+// entry and of product pb + 32U on return.  The batches' segment lookups do
+// not depend on each other (one shared load of 32 segment ends usually
+// places every batch start), so their latencies overlap.  Every lane must
+// call it.
+template <int U, typename T>
+struct NbStep {
+  int col[U];
+  T b[U], a[U];
+};
+
+template <int U, typename T>
+__device__ __forceinline__ void nb_load(const Csr& B, const T* __restrict__ bv, const int* off, const int* sstart,
+                                        const T* sa, int nseg, int tot, int hi, int pb, int& f, NbStep<U, T>& st) {
+  const int lane = lane_id();
+  auto end_of = [&](int g) {  // end of segment g + lane = start of the next one
+    const int nx = g + lane + 1;
+    return nx < nseg ? off[nx] : (nx == nseg ? tot : INT_MAX);
+  };
+  const int e0 = end_of(f);
+  int fu[U + 1];
+  fu[0] = f;
+#pragma unroll
+  for (int u = 1; u <= U; ++u) {
+    const int t = pb + 32 * u;
+    const int c = __popc(__ballot_sync(FULL, e0 <= t));
+    // more than 32 segments ahead: search (t < tot keeps the search valid)
+    fu[u] = c < 32 ? f + c : (t < tot ? nb_find_segment(off, nseg, t) : nseg);
   }
-  for (; t < len; t += 32) {
-    const int q = s + t;
-    const int jj = B.ci[q] - base;
-    if ((unsigned)jj < (unsigned)W) {
-      atomicOr(&bits[jj >> 5], 1u << (jj & 31));
-      atomicAdd(&acc[jj], a * bv[q]);
-    } else {
-      atomicOr(err, EB_UNSORTED);
+  f = fu[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int p0 = pb + 32 * u;
+    st.col[u] = 0;
+    st.b[u] = T(0);
+    st.a[u] = T(0);
+    if (p0 < hi) {  // warp-uniform
+      const int end = u == 0 ? e0 : end_of(fu[u]);
+      const int d = end == INT_MAX ? INT_MAX : end - p0;
+      const unsigned m = __reduce_or_sync(FULL, d <= 31 ? (1u << d) : 0u);
+      const int k = fu[u] + __popc(m & (lane == 31 ? FULL : ((2u << lane) - 1u)));
+      const int p = p0 + lane;
+      if (p < hi) {
+        const int q = sstart[k] + (p - off[k]);
+        st.col[u] = B.ci[q];
+        st.b[u] = bv[q];
+        st.a[u] = sa[k];
+      }
     }
   }
 }
 
+// The products [lo, hi) of the window's stream (tot products, nseg
+// segments), software-pipelined: the loads of the next step are in flight
+// while this step's products are accumulated.  hi - lo is a multiple of 32
+// unless hi == tot.  Every lane must call it.
+template <int W, typename T>
+__device__ __forceinline__ void nb_range(const Csr& B, const T* __restrict__ bv, const int* off, const int* sstart,
+                                         const T* sa, int nseg, int tot, int lo, int hi, int base, T* acc,
+                                         uint32_t* bits, uint32_t* err) {
+  constexpr int U = 2;
+  const int lane = lane_id();
+  int f = nb_find_segment(off, nseg, lo);
+  NbStep<U, T> cur;
+  nb_load<U, T>(B, bv, off, sstart, sa, nseg, tot, hi, lo, f, cur);
+  for (int p0 = lo; p0 < hi; p0 += 32 * U) {
+    NbStep<U, T> nxt;
+    if (p0 + 32 * U < hi) nb_load<U, T>(B, bv, off, sstart, sa, nseg, tot, hi, p0 + 32 * U, f, nxt);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (p0 + 32 * u + lane < hi) {
+        const int j = cur.col[u] - base;
+        if ((unsigned)j < (unsigned)W) {
+          atomicOr(&bits[j >> 5], 1u << (j & 31));
+          red_add_shared(&acc[j], cur.a[u] * cur.b[u]);
+        } else {
+          atomicOr(err, EB_UNSORTED);
+        }
+      }
+    }
+    cur = nxt;
+  }
+}
+
+// Appends the segments of a warp's 32 nonzeros (len 0: none) to the list:
+// one reservation per warp gives consecutive list entries and consecutive
+// stream offsets.  Every lane must call it.
+template <typename T>
+__device__ __forceinline__ void nb_append(unsigned long long* pk, int s, int len, T a, int* seg_off, int* seg_s,
+                                          T* seg_a) {
+  const int lane = lane_id();
+  const unsigned has = __ballot_sync(FULL, len > 0);
+  if (!has) return;
+  const int incl = warp_incl_scan(len);
+  const int tot = __shfl_sync(FULL, incl, 31);
+  unsigned long long at = 0ull;
+  if (lane == 0) at = atomicAdd(pk, ((unsigned long long)__popc(has) << 32) | (unsigned)tot);
+  at = __shfl_sync(FULL, at, 0);
+  if (len > 0) {
+    const int k = (int)(at >> 32) + __popc(has & lanemask_lt());
+    seg_off[k] = (int)(unsigned)(at & 0xffffffffull) + incl - len;
+    seg_s[k] = s;
+    seg_a[k] = a;
+  }
+}
+
+// Emits a warp's share of the window (bitmap words [w0, w0 + nw), nw <= 32)
+// at rci/rcv + pos0 in column order and clears it.  Lanes take consecutive
+// output positions, so the stores of C are coalesced: the owner word of a
+// position comes from a prefix of the words' popcounts, the bit from a
+// binary search on popcounts inside the word.  Every lane must call it.
+template <typename T>
+__device__ __forceinline__ void nb_emit(uint32_t* bits, T* acc, int w0, int nw, int base, int pos0, int out_end,
+                                        int32_t* __restrict__ rci, T* __restrict__ rcv, uint32_t* err) {
+  const int lane = lane_id();
+  const uint32_t m = lane < nw ? bits[w0 + lane] : 0u;
+  const int c = __popc(m);
+  const int inc = warp_incl_scan(c);
+  const int tot = __shfl_sync(FULL, inc, 31);
+  const int exc = inc - c;
+  for (int t0 = 0; t0 < tot; t0 += 32) {
+    const int t = t0 + lane;
+    const int o = warp_owner(inc, t);
+    const uint32_t mo = __shfl_sync(FULL, m, o & 31);
+    const int eo = __shfl_sync(FULL, exc, o & 31);
+    if (t < tot) {
+      // position of set bit number t - eo of mo
+      uint32_t x = mo;
+      int rank = t - eo, bit = 0;
+#pragma unroll
+      for (int sh = 16; sh >= 1; sh >>= 1) {
+        const int lowc = __popc(x & ((1u << sh) - 1u));
+        if (rank >= lowc) {
+          rank -= lowc;
+          x >>= sh;
+          bit += sh;
+        }
+      }
+      const int jj = ((w0 + o) << 5) + bit;
+      const int pos = pos0 + t;
+      const T v = acc[jj];
+      acc[jj] = T(0);
+      if (pos < out_end) {
+        __stcs(rci + pos, base + jj);
+        __stcs(rcv + pos, v);
+      } else {
+        atomicOr(err, EB_INTERNAL);
+      }
+    }
+  }
+  if (m) bits[w0 + lane] = 0u;
+}
+
+// rrb/runsb: B's run list at the block window's granularity (log2 W), so the
+// segment of B(k,:) in a block window is exactly one run.
 template <int W, int NW, typename T>
 __global__ void __launch_bounds__(NW * 32)
 k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri, const DevStats* st,
-            int bin_lo, int bin_hi, const int32_t* __restrict__ rr, const int2* __restrict__ runs, int run_shift,
-            int32_t* __restrict__ gcur, int32_t* __restrict__ gnxt, const int32_t* __restrict__ c_rp,
-            int32_t* __restrict__ c_ci, T* __restrict__ c_v, unsigned* counter, uint32_t* err) {
+            int bin_lo, int bin_hi, const int32_t* __restrict__ rrb, const int2* __restrict__ runsb,
+            int32_t* __restrict__ gcur, const int32_t* __restrict__ c_rp, int32_t* __restrict__ c_ci,
+            T* __restrict__ c_v, unsigned* counter, uint32_t* err) {
   static_assert(W % 1024 == 0, "window must be a multiple of 1024 columns");
   constexpr int NWORDS = W / 32;
+  constexpr int WPW = NWORDS / NW;  // bitmap words emitted per warp
+  static_assert(WPW >= 1 && WPW <= 32, "one bitmap word per lane at most");
+  constexpr int SEGCAP = nb_segcap<NW>();
+  static_assert(SEGCAP <= 1024, "the segment search covers 32 x 32 entries");
+  static_assert(SEGCAP >= NW * 32, "a row with register cursors fits one round");
+  constexpr int WSHIFT = (W == 2048) ? 11 : (W == 4096) ? 12 : (W == 8192) ? 13 : 14;
+  static_assert((1 << WSHIFT) == W, "window must be 2048, 4096, 8192 or 16384 columns");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* acc = reinterpret_cast<T*>(smem_raw);
-  uint32_t* bits = reinterpret_cast<uint32_t*>(smem_raw + (size_t)W * sizeof(T));
-  int* wcnt = reinterpret_cast<int*>(bits + NWORDS);
+  T* seg_a = acc + W;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(seg_a + SEGCAP);
+  int* seg_off = reinterpret_cast<int*>(bits + NWORDS);
+  int* seg_s = seg_off + SEGCAP;
+  int* wcnt = seg_s + SEGCAP;
   int* wnext = wcnt + NW;
-  NbPiece<T>* queue = reinterpret_cast<NbPiece<T>*>(
-      smem_raw + (((size_t)W * sizeof(T) + (size_t)NWORDS * 4 + (size_t)NW * 8 + 16 + 15) & ~(size_t)15));
-  __shared__ int s_lb, s_le, s_item, s_qn, s_qtake;
+  __shared__ int s_lb, s_le, s_item;
+  // (segments << 32) | products collected so far in a round; two of them, so
+  // one can be cleared while the other is read
+  __shared__ unsigned long long s_pack[2];
   const int warp = threadIdx.x >> 5, lane = lane_id();
   for (int t = threadIdx.x; t < W; t += NW * 32) acc[t] = T(0);
   for (int t = threadIdx.x; t < NWORDS; t += NW * 32) bits[t] = 0u;
   if (threadIdx.x == 0) {
     bin_range(st, bin_lo, bin_hi, &s_lb, &s_le);
-    s_qn = 0;
-    s_qtake = 0;
+    s_pack[0] = 0ull;
+    s_pack[1] = 0ull;
   }
   if (block_skip(st)) return;
   const int lb = s_lb, le = s_le;
-  const int wshift = 31 - __clz(W);      // block window width
-  const int rper = W >> run_shift;       // run windows of B per block window
+  int parity = 0;  // which s_pack the current round uses
 
   while (true) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
@@ -113,144 +260,105 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
     if (idx >= le) break;
     const int r = ri.rows[idx];
     const long long i = ri.row_begin + r;
-    const int a0 = A.rp[i], a1 = A.rp[i + 1], nA = a1 - a0;
+    const int a0 = A.rp[i], a1 = A.rp[i + 1];
     const int cmx = ri.cmax[r];
     const long long rbeg = c_rp[r];
     const int out_end = (int)(c_rp[r + 1] - rbeg);
     int32_t* const rci = c_ci + rbeg;
     T* const rcv = c_v + rbeg;
-    const int CS = min(32, max(1, (nA + NW - 1) / NW));  // nonzeros per chunk
-    const int nch = (nA + CS - 1) / CS;
-    // cursor of every nonzero: index of its current run in B's run list;
-    // gnxt holds that run's window id (INT_MAX when the B row is done)
+    // Cursor of a nonzero: index of its current run in the block-granular run
+    // list.  Up to 32 * NW nonzeros keep it in registers (thread t owns
+    // nonzero a0 + t) together with the run after it, loaded one window
+    // ahead; longer rows keep the index in gcur (parallel to A's nonzeros)
+    // and walk in rounds of SEGCAP nonzeros.
+    const bool regc = a1 - a0 <= NW * 32;  // block-uniform
+    int rj = 0;
+    int2 rcur = make_int2(INT_MAX, 0), rnxt = make_int2(INT_MAX, 0);
+    T ra = T(0);
     int mn = INT_MAX;
-    for (int c = warp; c < nch; c += NW) {
-      const int e = a0 + c * CS + lane;
-      if (lane < CS && e < a1) {
-        const int j = rr[A.ci[e]];
-        const int wid = runs[j].x;
+    if (regc) {
+      const int e = a0 + threadIdx.x;
+      if (e < a1) {
+        rj = rrb[A.ci[e]];
+        rcur = runsb[rj];
+        rnxt = runsb[rj + 1];  // past a row's sentinel: padding or the next row, never used
+        ra = av[e];
+        mn = rcur.x;
+      }
+    } else {
+      for (int e = a0 + threadIdx.x; e < a1; e += NW * 32) {
+        const int j = rrb[A.ci[e]];
         gcur[e] = j;
-        gnxt[e] = wid;
-        mn = min(mn, wid);
+        mn = min(mn, runsb[j].x);
       }
     }
     mn = warp_min(mn);
     if (lane == 0) wnext[warp] = mn;
     __syncthreads();
-    const int dshift = wshift - run_shift;  // run windows per block window = 2^dshift
-    int wb = INT_MAX;  // block window index
+    int wb = INT_MAX;  // block window index (the run list's window id)
     for (int w = 0; w < NW; ++w) wb = min(wb, wnext[w]);
-    if (wb != INT_MAX) wb >>= dshift;
     int out = 0;
     while (wb != INT_MAX) {
-      const int base = wb << wshift;
-      const int wlim = (wb + 1) * rper;  // first run window id past this block window
+      const int base = wb << WSHIFT;
       mn = INT_MAX;
-      for (int c = warp; c < nch; c += NW) {
-        const int e = a0 + c * CS + lane;
-        int s = 0, len = 0;
-        T a = T(0);
-        if (lane < CS && e < a1) {
-          int wid = gnxt[e];
-          if (wid < wlim) {
-            int j = gcur[e];
-            s = runs[j].y;
-            do {  // consecutive runs of this B row inside the block window
-              ++j;
-              wid = runs[j].x;
-            } while (wid < wlim);
-            len = runs[j].y - s;
-            gcur[e] = j;
-            gnxt[e] = wid;
-            a = av[e];
+      for (int r0 = a0; r0 < a1; r0 += SEGCAP) {  // one round with register cursors
+        const int r1 = min(a1, r0 + SEGCAP);
+        unsigned long long* pk = &s_pack[parity];
+        if (regc) {
+          int s = 0, len = 0;
+          if (rcur.x == wb) {
+            s = rcur.y;
+            len = rnxt.y - s;
+            ++rj;
+            rcur = rnxt;
+            rnxt = runsb[rj + 1];  // in flight until a later window needs it
           }
-          mn = min(mn, wid);
-        }
-        // very long segments: queue their pieces for all warps (warp-aggregated
-        // reservation); if the queue is full the warp keeps the segment
-        bool keep = len >= 32;
-        if (len >= NB_LONG) {
-          const int np = (len + NB_PIECE - 1) / NB_PIECE;
-          const int at = atomicAdd(&s_qn, np);  // reserve np slots
-          if (at + np <= NB_QCAP) {
-            for (int p = 0; p < np; ++p) {
-              NbPiece<T> pc;
-              pc.s = s + p * NB_PIECE;
-              pc.len = min(NB_PIECE, len - p * NB_PIECE);
-              pc.a = a;
-              queue[at + p] = pc;
+          mn = min(mn, rcur.x);
+          nb_append<T>(pk, s, len, ra, seg_off, seg_s, seg_a);
+        } else {
+          for (int e0 = r0 + warp * 32; e0 < r1; e0 += NW * 32) {
+            const int e = e0 + lane;
+            int s = 0, len = 0;
+            T a = T(0);
+            if (e < r1) {
+              const int j = gcur[e];
+              const int2 c0 = runsb[j], c1 = runsb[j + 1];
+              if (c0.x == wb) {
+                s = c0.y;
+                len = c1.y - s;
+                a = av[e];
+                gcur[e] = j + 1;
+                mn = min(mn, c1.x);
+              } else {
+                mn = min(mn, c0.x);
+              }
             }
-            keep = false;
-          } else {
-            // queue full: the slots reserved below the capacity stay empty
-            for (int p = at; p < NB_QCAP && p < at + np; ++p) {
-              NbPiece<T> pc;
-              pc.s = 0;
-              pc.len = 0;
-              pc.a = T(0);
-              queue[p] = pc;
-            }
+            nb_append<T>(pk, s, len, a, seg_off, seg_s, seg_a);
           }
         }
-        // remaining long segments by the whole warp, short ones flattened
-        unsigned lm = __ballot_sync(FULL, keep);
-        while (lm) {
-          const int L = __ffs(lm) - 1;
-          lm &= lm - 1;
-          const int ls = __shfl_sync(FULL, s, L), ln = __shfl_sync(FULL, len, L);
-          const T la = __shfl_sync(FULL, a, L);
-          nb_piece<W, T>(B, bv, ls, ln, la, base, acc, bits, err);
+        __syncthreads();  // the list is complete
+        const unsigned long long pv = *pk;
+        const int nseg = (int)(pv >> 32), tot = (int)(unsigned)(pv & 0xffffffffull);
+        if (threadIdx.x == 0) s_pack[parity ^ 1] = 0ull;  // for the next round
+        {  // each warp takes a contiguous share of the stream, whole batches
+          const int share = ((tot + NW * 32 - 1) / (NW * 32)) * 32;
+          const int lo = warp * share, hi = min(tot, lo + share);
+          if (lo < hi) nb_range<W, T>(B, bv, seg_off, seg_s, seg_a, nseg, tot, lo, hi, base, acc, bits, err);
         }
-        const int sl = len < 32 ? len : 0;
-        const int incl = warp_incl_scan(sl);
-        const int tot = __shfl_sync(FULL, incl, 31);
-        const int excl = incl - sl;
-        for (int p0 = 0; p0 < tot; p0 += 32) {
-          const int p = p0 + lane;
-          const int o = warp_owner(incl, p);
-          const int os = __shfl_sync(FULL, s, o), oex = __shfl_sync(FULL, excl, o);
-          const T oa = __shfl_sync(FULL, a, o);
-          if (p < tot) {
-            const int q = os + p - oex;
-            const int jj = B.ci[q] - base;
-            if ((unsigned)jj < (unsigned)W) {
-              atomicOr(&bits[jj >> 5], 1u << (jj & 31));
-              atomicAdd(&acc[jj], oa * bv[q]);
-            } else {
-              atomicOr(err, EB_UNSORTED);
-            }
-          }
-        }
+        __syncthreads();  // all products in; the list may be refilled
+        parity ^= 1;
       }
+      // emission: warp w takes bitmap words [w * WPW, (w + 1) * WPW)
       mn = warp_min(mn);
-      __syncthreads();  // the queue is complete
-      {
-        const int qn = min(s_qn, NB_QCAP);
-        while (true) {
-          int pi = 0;
-          if (lane == 0) pi = atomicAdd(&s_qtake, 1);
-          pi = __shfl_sync(FULL, pi, 0);
-          if (pi >= qn) break;
-          const NbPiece<T> pc = queue[pi];
-          nb_piece<W, T>(B, bv, pc.s, pc.len, pc.a, base, acc, bits, err);
-        }
-      }
-      // emission: each warp takes NWORDS / NW consecutive words of the bitmap
       const int ncols = min(W, cmx - base + 1);
       const int nwd = (ncols + 31) >> 5;
-      constexpr int WPW = NWORDS / NW;
-      __syncthreads();  // all products are in
       const int w0 = warp * WPW;
-      int cnt = 0;
-      for (int j = w0 + lane; j < w0 + WPW && j < nwd; j += 32) cnt += __popc(bits[j]);
+      const int nw = max(0, min(WPW, nwd - w0));
+      int cnt = lane < nw ? __popc(bits[w0 + lane]) : 0;
       cnt = warp_sum(cnt);
       if (lane == 0) {
         wcnt[warp] = cnt;
         wnext[warp] = mn;
-      }
-      if (threadIdx.x == 0) {  // queue drained by everyone (all past the barrier above)
-        s_qn = 0;
-        s_qtake = 0;
       }
       __syncthreads();
       int before = 0, total = 0, nb = INT_MAX;
@@ -260,32 +368,10 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
         total += v;
         nb = min(nb, wnext[w]);
       }
-      int pos0 = out + before;
-      for (int jb = w0; jb < w0 + WPW && jb < nwd; jb += 32) {
-        const int j = jb + lane;
-        uint32_t m = (j < w0 + WPW && j < nwd) ? bits[j] : 0u;
-        const int c = __popc(m);
-        const int inc = warp_incl_scan(c);
-        int pos = pos0 + inc - c;
-        if (m) bits[j] = 0u;
-        while (m) {
-          const int b = __ffs(m) - 1;
-          m &= m - 1;
-          const int jj = (j << 5) + b;
-          if (pos < out_end) {
-            __stcs(rci + pos, base + jj);
-            __stcs(rcv + pos, acc[jj]);
-          } else {
-            atomicOr(err, EB_INTERNAL);
-          }
-          acc[jj] = T(0);
-          ++pos;
-        }
-        pos0 += __shfl_sync(FULL, inc, 31);
-      }
+      nb_emit<T>(bits, acc, w0, nw, base, out + before, out_end, rci, rcv, err);
       out += total;
-      __syncthreads();  // window cleared before the next one fills it
-      wb = nb == INT_MAX ? INT_MAX : (nb >> dshift);
+      __syncthreads();  // window cleared and counts read before the next window
+      wb = nb;
     }
     if (threadIdx.x == 0 && out != out_end) atomicOr(err, EB_INTERNAL);
   }

@@ -61,8 +61,9 @@ static cudaError_t block_num(const LaunchCtx& c, const Csr& A, const Csr& B, con
   unsigned* counter = &c.st->work[1];
   cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), c.stream);
   if (e != cudaSuccess) return e;
-  k<<<c.nsm * occ, NUM_BLOCK_WARPS * 32, smem, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, sp.rr, sp.runs,
-                                                          sp.wf_shift, cur, nxt, c_rp, c_ci, c_v, counter, c.err);
+  if (!sp.rrb || !sp.runsb || (1 << sp.wb_shift) != W) return cudaErrorInvalidValue;  // block-granular runs
+  k<<<c.nsm * occ, NUM_BLOCK_WARPS * 32, smem, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, sp.rrb, sp.runsb, cur,
+                                                          c_rp, c_ci, c_v, counter, c.err);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -113,15 +114,16 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
   if (hi >= blo) {
     timer_mark(c, T_NUM_BLOCK, 0);
 #define SG_BLOCK_NUM(WW, NWW) e = block_num<T, WW, NWW>(c, A, B, av, bv, ri, blo, hi, sp, cur, nxt, c_rp, c_ci, c_v)
-    if (tu.block_warps == 8) {
-      if (tu.window_block == 16384) SG_BLOCK_NUM(16384, 8);
-      else if (tu.window_block == 4096) SG_BLOCK_NUM(4096, 8);
-      else SG_BLOCK_NUM(8192, 8);
-    } else {
-      if (tu.window_block == 16384) SG_BLOCK_NUM(16384, 16);
-      else if (tu.window_block == 4096) SG_BLOCK_NUM(4096, 16);
-      else SG_BLOCK_NUM(8192, 16);
-    }
+    // supported geometries (window columns, warps); others fall back to 8192 x 8
+    const int wbk = tu.window_block, nwk = tu.block_warps;
+    if (wbk == 2048 && nwk == 4) SG_BLOCK_NUM(2048, 4);
+    else if (wbk == 2048 && nwk == 8) SG_BLOCK_NUM(2048, 8);
+    else if (wbk == 4096 && nwk == 4) SG_BLOCK_NUM(4096, 4);
+    else if (wbk == 4096 && nwk == 8) SG_BLOCK_NUM(4096, 8);
+    else if (wbk == 4096 && nwk == 16) SG_BLOCK_NUM(4096, 16);
+    else if (wbk == 16384 && nwk == 16) SG_BLOCK_NUM(16384, 16);
+    else if (wbk == 8192 && nwk == 16) SG_BLOCK_NUM(8192, 16);
+    else SG_BLOCK_NUM(8192, 8);
 #undef SG_BLOCK_NUM
     timer_mark(c, T_NUM_BLOCK, 1);
     if (e) return e;

@@ -71,7 +71,7 @@ struct WarpWin {
     if (act) {
       if ((unsigned)j < (unsigned)W) {
         mark(j);
-        atomicAdd(&acc[j], a * b);
+        red_add_shared(&acc[j], a * b);
       } else {
         atomicOr(err, EB_UNSORTED);
       }

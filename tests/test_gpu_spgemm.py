@@ -275,10 +275,10 @@ def test_register_sort_multi_slot(api, oracle_mod, P):
     assert_values_exact(C.vals, R.vals)
 
 
-@pytest.mark.parametrize("num_block_min", [256, 4096])
-def test_block_window_queue_overflow_and_long_segments(api, oracle_mod, num_block_min):
-    """Rows with thousands of long B segments per window (queue overflow) and
-    hub columns hit by every segment, through the block-window kernel."""
+BLOCK_GEOMETRIES = [(2048, 4), (2048, 8), (4096, 4), (4096, 8), (4096, 16), (8192, 8), (8192, 16), (16384, 16)]
+
+
+def _hub_workload():
     rng = np.random.default_rng(17)
     counts = rng.integers(50, 800, size=40)
     counts[:3] = [2000, 1500, 1200]
@@ -293,7 +293,36 @@ def test_block_window_queue_overflow_and_long_segments(api, oracle_mod, num_bloc
     ci = np.concatenate(rows).astype(np.int32)
     nrp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
     B = gen.CSR(B.nrows, B.ncols, nrp, ci, rng.integers(-3, 4, len(ci)).astype(np.float64))
+    return A, B
+
+
+@pytest.mark.parametrize("num_block_min", [256, 4096])
+def test_block_window_long_rows_and_hub_columns(api, oracle_mod, num_block_min):
+    """Rows of up to 2000 nonzeros (cursors in global memory, several rounds
+    of segments per window) next to short ones (cursors in registers), long
+    B segments and hub columns hit by every segment, through the
+    block-window kernel; integer values, so the sums are exact."""
+    A, B = _hub_workload()
     C, _ = run(api, A, B, num_block_min=num_block_min)
+    R = oracle_mod.spgemm(A, B)
+    assert_structure_equal(C, R)
+    assert_values_exact(C.vals, R.vals)
+
+
+@pytest.mark.parametrize("geom", BLOCK_GEOMETRIES)
+def test_block_window_geometries(api, oracle_mod, geom):
+    """Every compiled (window columns, warps) pair of the block kernel."""
+    A, B = _hub_workload()
+    C, _ = run(api, A, B, num_block_min=256, window_block=geom[0], block_warps=geom[1])
+    R = oracle_mod.spgemm(A, B)
+    assert_structure_equal(C, R)
+    assert_values_exact(C.vals, R.vals)
+
+
+def test_block_window_fp32_exact(api, oracle_mod):
+    """FP32 through the block kernel: integer sums below 2**24 are exact."""
+    A, B = _hub_workload()
+    C, _ = run(api, A, B, dtype=torch.float32, num_block_min=256)
     R = oracle_mod.spgemm(A, B)
     assert_structure_equal(C, R)
     assert_values_exact(C.vals, R.vals)
