@@ -42,7 +42,8 @@ __host__ __device__ constexpr size_t numblock_smem_bytes() {
          + (size_t)nb_segcap<NW>() * sizeof(T)  // segment multipliers A(i,k)
          + (size_t)(W / 32) * 4                // presence bitmap
          + (size_t)nb_segcap<NW>() * 8         // segment stream offsets and starts in B
-         + (size_t)NW * 8;                     // per-warp counts and next windows
+         + (size_t)NW * 8                      // per-warp counts and next windows
+         + (size_t)(W / 32) * 4;               // per-word output offsets inside a warp's share
 }
 
 // Last segment k in [0, nseg) whose stream offset is <= p (offsets strictly
@@ -164,29 +165,38 @@ __device__ __forceinline__ void nb_append(unsigned long long* pk, int s, int len
   }
 }
 
-// Emits a warp's share of the window (bitmap words [w0, w0 + nw), nw <= 32)
-// at rci/rcv + pos0 in column order and clears it.  Lanes take consecutive
-// output positions, so the stores of C are coalesced: the owner word of a
-// position comes from a prefix of the words' popcounts, the bit from a
-// binary search on popcounts inside the word.  Every lane must call it.
-template <typename T>
-__device__ __forceinline__ void nb_emit(uint32_t* bits, T* acc, int w0, int nw, int base, int pos0, int out_end,
-                                        int32_t* __restrict__ rci, T* __restrict__ rcv, uint32_t* err) {
-  const int lane = lane_id();
-  const uint32_t m = lane < nw ? bits[w0 + lane] : 0u;
-  const int c = __popc(m);
-  const int inc = warp_incl_scan(c);
-  const int tot = __shfl_sync(FULL, inc, 31);
-  const int exc = inc - c;
-  for (int t0 = 0; t0 < tot; t0 += 32) {
+// Emission of a window in column order, balanced over the block's warps by
+// output count.  Bitmap words are grouped in NW chunks of WPW words (chunk w
+// was popcounted by warp w: wpre holds each word's exclusive offset inside its
+// chunk, wcnt the chunk totals).  The window's outputs are cut into NW equal
+// contiguous shares; lanes take consecutive outputs, so the stores of C are
+// coalesced.  An output's chunk comes from a warp search over the chunk
+// offsets, its word from a binary search over the chunk's offsets, its bit
+// from a binary search on popcounts inside the word.  Every lane must call it.
+template <int NW, int WPW, typename T>
+__device__ __forceinline__ void nb_emit(const uint32_t* bits, const int* wpre, const int* wcnt, T* acc, int base,
+                                        int out, int out_end, int32_t* __restrict__ rci, T* __restrict__ rcv,
+                                        uint32_t* err) {
+  const int lane = lane_id(), warp = threadIdx.x >> 5;
+  const int cnt = lane < NW ? wcnt[lane] : 0;
+  const int cinc = warp_incl_scan(cnt);  // chunk ends (lanes >= NW repeat the total)
+  const int total = __shfl_sync(FULL, cinc, 31);
+  const int share = ((total + NW * 32 - 1) / (NW * 32)) * 32;
+  const int lo = warp * share, hi = min(total, lo + share);
+  for (int t0 = lo; t0 < hi; t0 += 32) {
     const int t = t0 + lane;
-    const int o = warp_owner(inc, t);
-    const uint32_t mo = __shfl_sync(FULL, m, o & 31);
-    const int eo = __shfl_sync(FULL, exc, o & 31);
-    if (t < tot) {
-      // position of set bit number t - eo of mo
-      uint32_t x = mo;
-      int rank = t - eo, bit = 0;
+    const int c = warp_owner(cinc, t);  // chunk of output t
+    const int coff = __shfl_sync(FULL, cinc - cnt, c & 31);
+    if (t < hi) {
+      const int rel = t - coff;
+      const int* pre = wpre + c * WPW;
+      int wj = 0;  // last word of the chunk whose offset is <= rel
+#pragma unroll
+      for (int sh = 16; sh >= 1; sh >>= 1)
+        if (sh < WPW && wj + sh < WPW && pre[wj + sh] <= rel) wj += sh;
+      const int word = c * WPW + wj;
+      uint32_t x = bits[word];
+      int rank = rel - pre[wj], bit = 0;
 #pragma unroll
       for (int sh = 16; sh >= 1; sh >>= 1) {
         const int lowc = __popc(x & ((1u << sh) - 1u));
@@ -196,8 +206,8 @@ __device__ __forceinline__ void nb_emit(uint32_t* bits, T* acc, int w0, int nw, 
           bit += sh;
         }
       }
-      const int jj = ((w0 + o) << 5) + bit;
-      const int pos = pos0 + t;
+      const int jj = (word << 5) + bit;
+      const int pos = out + t;
       const T v = acc[jj];
       acc[jj] = T(0);
       if (pos < out_end) {
@@ -208,7 +218,6 @@ __device__ __forceinline__ void nb_emit(uint32_t* bits, T* acc, int w0, int nw, 
       }
     }
   }
-  if (m) bits[w0 + lane] = 0u;
 }
 
 // rrb/runsb: B's run list at the block window's granularity (log2 W), so the
@@ -236,6 +245,7 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
   int* seg_s = seg_off + SEGCAP;
   int* wcnt = seg_s + SEGCAP;
   int* wnext = wcnt + NW;
+  int* wpre = wnext + NW;
   __shared__ int s_lb, s_le, s_item;
   // (segments << 32) | products collected so far in a round; two of them, so
   // one can be cleared while the other is read
@@ -348,29 +358,31 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
         __syncthreads();  // all products in; the list may be refilled
         parity ^= 1;
       }
-      // emission: warp w takes bitmap words [w * WPW, (w + 1) * WPW)
+      // emission: warp w popcounts bitmap words [w * WPW, (w + 1) * WPW), then
+      // all warps emit equal shares of the window's outputs
       mn = warp_min(mn);
       const int ncols = min(W, cmx - base + 1);
       const int nwd = (ncols + 31) >> 5;
       const int w0 = warp * WPW;
-      const int nw = max(0, min(WPW, nwd - w0));
-      int cnt = lane < nw ? __popc(bits[w0 + lane]) : 0;
-      cnt = warp_sum(cnt);
-      if (lane == 0) {
-        wcnt[warp] = cnt;
+      const int wi = w0 + lane;
+      const uint32_t myw = (lane < WPW && wi < nwd) ? bits[wi] : 0u;
+      const int c = __popc(myw);
+      const int inc = warp_incl_scan(c);
+      if (lane < WPW) wpre[wi] = inc - c;
+      if (lane == 31) {
+        wcnt[warp] = inc;
         wnext[warp] = mn;
       }
       __syncthreads();
-      int before = 0, total = 0, nb = INT_MAX;
+      int total = 0, nb = INT_MAX;
       for (int w = 0; w < NW; ++w) {
-        const int v = wcnt[w];
-        if (w < warp) before += v;
-        total += v;
+        total += wcnt[w];
         nb = min(nb, wnext[w]);
       }
-      nb_emit<T>(bits, acc, w0, nw, base, out + before, out_end, rci, rcv, err);
+      nb_emit<NW, WPW, T>(bits, wpre, wcnt, acc, base, out, out_end, rci, rcv, err);
       out += total;
-      __syncthreads();  // window cleared and counts read before the next window
+      __syncthreads();  // every warp is done reading bits, wpre and wcnt
+      if (myw) bits[wi] = 0u;
       wb = nb;
     }
     if (threadIdx.x == 0 && out != out_end) atomicOr(err, EB_INTERNAL);
