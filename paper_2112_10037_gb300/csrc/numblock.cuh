@@ -24,7 +24,7 @@
 // wide sparse row needs that many times fewer windows.
 #pragma once
 
-#include "internal.cuh"
+#include "segstream.cuh"
 
 namespace sg {
 
@@ -44,18 +44,6 @@ __host__ __device__ constexpr size_t numblock_smem_bytes() {
          + (size_t)nb_segcap<NW>() * 8         // segment stream offsets and starts in B
          + (size_t)NW * 8                      // per-warp counts and next windows
          + (size_t)(W / 32) * 4;               // per-word output offsets inside a warp's share
-}
-
-// Last segment k in [0, nseg) whose stream offset is <= p (offsets strictly
-// increase, off[0] == 0 <= p, nseg <= 1024): two 32-way steps.
-__device__ __forceinline__ int nb_find_segment(const int* off, int nseg, int p) {
-  const int lane = lane_id();
-  int idx = lane * 32;
-  unsigned b = __ballot_sync(FULL, idx < nseg && off[idx] <= p);
-  const int f1 = (31 - __clz(b)) * 32;
-  idx = f1 + lane;
-  b = __ballot_sync(FULL, idx < nseg && off[idx] <= p);
-  return f1 + (31 - __clz(b));
 }
 
 // Loads of one step of U batches of 32 products from pb on: column, B value
@@ -86,7 +74,7 @@ __device__ __forceinline__ void nb_load(const Csr& B, const T* __restrict__ bv, 
     const int t = pb + 32 * u;
     const int c = __popc(__ballot_sync(FULL, e0 <= t));
     // more than 32 segments ahead: search (t < tot keeps the search valid)
-    fu[u] = c < 32 ? f + c : (t < tot ? nb_find_segment(off, nseg, t) : nseg);
+    fu[u] = c < 32 ? f + c : (t < tot ? seg_find(off, nseg, t) : nseg);
   }
   f = fu[U];
 #pragma unroll
@@ -121,7 +109,7 @@ __device__ __forceinline__ void nb_range(const Csr& B, const T* __restrict__ bv,
                                          uint32_t* bits, uint32_t* err) {
   constexpr int U = 2;
   const int lane = lane_id();
-  int f = nb_find_segment(off, nseg, lo);
+  int f = seg_find(off, nseg, lo);
   NbStep<U, T> cur;
   nb_load<U, T>(B, bv, off, sstart, sa, nseg, tot, hi, lo, f, cur);
   for (int p0 = lo; p0 < hi; p0 += 32 * U) {
@@ -140,28 +128,6 @@ __device__ __forceinline__ void nb_range(const Csr& B, const T* __restrict__ bv,
       }
     }
     cur = nxt;
-  }
-}
-
-// Appends the segments of a warp's 32 nonzeros (len 0: none) to the list:
-// one reservation per warp gives consecutive list entries and consecutive
-// stream offsets.  Every lane must call it.
-template <typename T>
-__device__ __forceinline__ void nb_append(unsigned long long* pk, int s, int len, T a, int* seg_off, int* seg_s,
-                                          T* seg_a) {
-  const int lane = lane_id();
-  const unsigned has = __ballot_sync(FULL, len > 0);
-  if (!has) return;
-  const int incl = warp_incl_scan(len);
-  const int tot = __shfl_sync(FULL, incl, 31);
-  unsigned long long at = 0ull;
-  if (lane == 0) at = atomicAdd(pk, ((unsigned long long)__popc(has) << 32) | (unsigned)tot);
-  at = __shfl_sync(FULL, at, 0);
-  if (len > 0) {
-    const int k = (int)(at >> 32) + __popc(has & lanemask_lt());
-    seg_off[k] = (int)(unsigned)(at & 0xffffffffull) + incl - len;
-    seg_s[k] = s;
-    seg_a[k] = a;
   }
 }
 
@@ -324,7 +290,7 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
             rnxt = runsb[rj + 1];  // in flight until a later window needs it
           }
           mn = min(mn, rcur.x);
-          nb_append<T>(pk, s, len, ra, seg_off, seg_s, seg_a);
+          seg_append<T>(pk, s, len, ra, seg_off, seg_s, seg_a);
         } else {
           for (int e0 = r0 + warp * 32; e0 < r1; e0 += NW * 32) {
             const int e = e0 + lane;
@@ -343,7 +309,7 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
                 mn = min(mn, c0.x);
               }
             }
-            nb_append<T>(pk, s, len, a, seg_off, seg_s, seg_a);
+            seg_append<T>(pk, s, len, a, seg_off, seg_s, seg_a);
           }
         }
         __syncthreads();  // the list is complete

@@ -2,13 +2,14 @@
 // (Sec. 2.2: the union of the columns of the B rows a row of A touches).
 #include "launch_util.cuh"
 #include "rowpass.cuh"
+#include "symblock.cuh"
 
 namespace sg {
 
 // Symbolic windows hold only a presence bitmap, so they are wide.
 constexpr int SYM_WARP_W = 32768;    // 4 KB of bits per warp
 constexpr int SYM_BLOCK_W = 262144;  // 32 KB of bits per block
-constexpr int SYM_BLOCK_WARPS = 16;
+constexpr int SYM_BLOCK_WARPS = 8;
 
 static long long rows_in(const int* path_rows, int p) { return path_rows ? path_rows[p] : -1; }
 
@@ -55,6 +56,21 @@ static cudaError_t window_sym(const LaunchCtx& c, const Csr& A, const Csr& B, co
   return cudaGetLastError();
 }
 
+template <int W, int NW>
+static cudaError_t block_sym(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri, int lo, int hi,
+                             const SplitInfo& sp, int32_t* cursor, int32_t* c_cnt) {
+  auto k = k_sym_block<W, NW>;
+  const size_t smem = symblock_smem_bytes<W, NW>();
+  const int occ = kernel_blocks_per_sm(k, NW * 32, smem);
+  if (occ <= 0) return cudaErrorInvalidConfiguration;
+  unsigned* counter = &c.st->work[2];
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), c.stream);
+  if (e != cudaSuccess) return e;
+  k<<<c.nsm * occ, NW * 32, smem, c.stream>>>(A, B, ri, c.st, lo, hi, sp, cursor, c_cnt, counter, c.err);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_symbolic(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
                             const PathBins& pb, const Tuning& tu, const SplitInfo& sp, int32_t* cursor,
                             int32_t* c_cnt, const int* path_rows) {
@@ -81,8 +97,7 @@ cudaError_t launch_symbolic(const LaunchCtx& c, const Csr& A, const Csr& B, cons
   }
   if (pb.hi[PATH_BLOCK] >= pb.lo[PATH_BLOCK]) {
     timer_mark(c, T_SYM_BLOCK, 0);
-    e = window_sym<SYM_BLOCK_WARPS, SYM_BLOCK_WARPS, SYM_BLOCK_W>(c, A, B, ri, pb.lo[PATH_BLOCK], pb.hi[PATH_BLOCK],
-                                                                 sp, cursor, c_cnt, rows_in(path_rows, PATH_BLOCK));
+    e = block_sym<SYM_BLOCK_W, SYM_BLOCK_WARPS>(c, A, B, ri, pb.lo[PATH_BLOCK], pb.hi[PATH_BLOCK], sp, cursor, c_cnt);
     timer_mark(c, T_SYM_BLOCK, 1);
     if (e) return e;
   }
