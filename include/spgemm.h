@@ -130,6 +130,23 @@ spgemm_status spgemm_analyse(const spgemm_csr* A, const spgemm_csr* B,
                              size_t workspace_bytes, spgemm_stream_t stream,
                              spgemm_plan** plan);
 
+/* Row-range plans sharing one preprocessing of B.  Rows of C are independent
+ * (Sec. 2.2: row i of C depends only on row i of A), so C can be produced in
+ * row ranges, for example to copy one range to the host while the next is
+ * computed.  spgemm_analyse_rows creates a plan for rows [row_begin, row_end)
+ * of base's product (C then has row_end - row_begin rows) that reads base's
+ * window-run lists of B instead of building its own; its options are base's
+ * (validate and backward off).  base must have been analysed on `stream`
+ * (or work ordered before it) and must outlive the new plan; A, B and base's
+ * workspace must stay unchanged.  spgemm_rows_workspace_size gives the
+ * workspace the new plan needs.  SPGEMM_ERR_DIM_MISMATCH for a range outside
+ * [0, nrows(A)].  Does not block. */
+spgemm_status spgemm_rows_workspace_size(const spgemm_plan* base, int64_t row_begin,
+                                         int64_t row_end, size_t* bytes);
+spgemm_status spgemm_analyse_rows(const spgemm_plan* base, int64_t row_begin, int64_t row_end,
+                                  void* workspace, size_t workspace_bytes,
+                                  spgemm_stream_t stream, spgemm_plan** plan);
+
 /* Symbolic pass: sizes every row of C (the number of distinct columns the
  * row's products reach, Sec. 2.2) and writes C's row pointer to c_row_ptr
  * (device, int32, nrows(C)+1 entries) by an exclusive prefix sum.  BLOCKS on

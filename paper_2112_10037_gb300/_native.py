@@ -60,6 +60,10 @@ _SIG = {
                                ctypes.POINTER(spgemm_opts), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "spgemm_analyse": ([ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_opts),
                         _P, ctypes.c_size_t, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "spgemm_rows_workspace_size": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "spgemm_analyse_rows": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t,
+                             ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "spgemm_symbolic": ([_P, _P, _I64P, _P], ctypes.c_int),
     "spgemm_numeric": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "spgemm_plan_stats": ([_P, _P, _I64P, _I64P, _I64P], ctypes.c_int),
@@ -139,6 +143,22 @@ def spgemm_analyse(A: spgemm_csr, B: spgemm_csr, opts: spgemm_opts, workspace: i
     _check(lib().spgemm_analyse(ctypes.byref(A), ctypes.byref(B), ctypes.byref(opts), _P(workspace),
                                 ctypes.c_size_t(workspace_bytes), _P(stream), ctypes.byref(plan)),
            "spgemm_analyse")
+    return plan.value
+
+
+def spgemm_rows_workspace_size(base: int, row_begin: int, row_end: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().spgemm_rows_workspace_size(_P(base), ctypes.c_int64(row_begin), ctypes.c_int64(row_end),
+                                            ctypes.byref(n)), "spgemm_rows_workspace_size")
+    return n.value
+
+
+def spgemm_analyse_rows(base: int, row_begin: int, row_end: int, workspace: int, workspace_bytes: int,
+                        stream: int) -> int:
+    plan = _P(None)
+    _check(lib().spgemm_analyse_rows(_P(base), ctypes.c_int64(row_begin), ctypes.c_int64(row_end), _P(workspace),
+                                     ctypes.c_size_t(workspace_bytes), _P(stream), ctypes.byref(plan)),
+           "spgemm_analyse_rows")
     return plan.value
 
 

@@ -104,6 +104,24 @@ class Plan:
         self.col_idx: Optional[torch.Tensor] = None
         self.nnz: Optional[int] = None
 
+    def rows(self, row_begin: int, row_end: int, stream=None) -> "Plan":
+        """Plan for rows [row_begin, row_end) of this product that reads this
+        plan's preprocessing of B (``spgemm_analyse_rows``), issuing on
+        ``stream`` (default: the current stream), which must be ordered after
+        this plan's analysis; this plan must outlive it."""
+        p = object.__new__(Plan)
+        p.A, p.B, p.dtype, p.stream = self.A, self.B, self.dtype, _stream_handle(stream)
+        p.opts = make_opts(dtype=self.dtype)
+        p._a, p._b = self._a, self._b
+        nbytes = nat.spgemm_rows_workspace_size(self.handle, row_begin, row_end)
+        p.workspace = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=self.workspace.device)
+        p.handle = nat.spgemm_analyse_rows(self.handle, row_begin, row_end, p.workspace.data_ptr(), nbytes,
+                                           p.stream)
+        p.nrows = row_end - row_begin
+        p.row_ptr, p.col_idx, p.nnz = None, None, None
+        p._base = self  # keeps the base plan alive
+        return p
+
     def symbolic(self):
         self.row_ptr = torch.empty(self.nrows + 1, dtype=torch.int32, device=self.workspace.device)
         self.nnz = nat.spgemm_symbolic(self.handle, self.row_ptr.data_ptr(), self.stream)
@@ -153,6 +171,93 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, dtype=None, **opt_kw) -> DeviceCSR:
     ci, v = plan.numeric(A.vals, B.vals)
     plan.close()
     return DeviceCSR(plan.nrows, B.ncols, rp, ci, v)
+
+
+_streams = {}
+
+
+def _stream_pool(dev, name, n):
+    key = (dev.index, name)
+    pool = _streams.get(key)
+    if pool is None or len(pool) < n:
+        pool = _streams[key] = [torch.cuda.Stream(device=dev) for _ in range(n)]
+    return pool[:n]
+
+
+def spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int = 4, streams: int = 1, out=None,
+                   **opt_kw):
+    """C = A*B with C delivered in pinned host memory.
+
+    Rows of C are independent (Sec. 2.2), so C is computed in ``chunks`` row
+    ranges of about equal shares of A's nonzeros, each a plan sharing one
+    preprocessing of B (``spgemm_analyse_rows``).  After all ranges are sized,
+    the ranges' numeric passes run on ``streams`` compute streams while a
+    copy stream brings finished ranges to the host, so the device-to-host
+    copy of C overlaps the computation; only the first range's computation
+    and the last range's copy are not hidden.  Each range waits for its own
+    longest rows, which one whole-matrix pass would overlap with other work,
+    so a few ranges (default 4, one compute stream) do best on power-law
+    matrices.  ``out`` = (row_ptr, col_idx, vals) pinned CPU tensors
+    to fill, reused when large enough.  Returns CPU tensors (row_ptr,
+    col_idx, vals); blocks until they are complete."""
+    dev = A.row_ptr.device
+    comp = torch.cuda.current_stream(dev)
+    copy = _stream_pool(dev, "copy", 1)[0]
+    work = _stream_pool(dev, "compute", max(1, int(streams)))
+    m = A.nrows
+    base = Plan(A, B, dtype=dtype, row_range=(0, 0), **opt_kw)  # B's run lists only
+    k = max(1, min(int(chunks), m))
+    targets = (torch.arange(1, k, device=dev, dtype=torch.int64) * A.nnz // k).to(torch.int32)
+    cuts = torch.searchsorted(A.row_ptr, targets).cpu().tolist() if k > 1 else []
+    bounds = sorted(set([0, m] + [min(max(int(c), 0), m) for c in cuts]))
+    ranges = [(rb, re) for rb, re in zip(bounds[:-1], bounds[1:]) if re > rb]
+    a_vals = A.vals.to(dtype)
+    b_vals = B.vals.to(dtype)
+    ready = torch.cuda.Event()
+    ready.record(comp)  # inputs, their values in dtype and B's run lists
+    for s in work:
+        s.wait_event(ready)
+    plans, nnzs = [], []
+    for i, (rb, re) in enumerate(ranges):
+        with torch.cuda.stream(work[i % len(work)]):  # the plan's workspace and C's row pointer live there
+            pl = base.rows(rb, re)
+            plans.append(pl)
+            nnzs.append(pl.symbolic()[1])
+    offs = np.concatenate([[0], np.cumsum(nnzs)]).astype(np.int64)
+    total = int(offs[-1])
+    if total >= 2**31:
+        raise nat.SpgemmError("nnz(C) does not fit int32")
+    if out is None or out[0].numel() < m + 1 or out[1].numel() < total or out[2].numel() < total:
+        out = (torch.empty(m + 1, dtype=torch.int32).pin_memory(),
+               torch.empty(max(total, 1), dtype=torch.int32).pin_memory(),
+               torch.empty(max(total, 1), dtype=dtype).pin_memory())
+    h_rp, h_ci, h_v = out
+    for idx in range(len(plans)):
+        pl, (rb, re) = plans[idx], ranges[idx]
+        o, n = int(offs[idx]), nnzs[idx]
+        ws = work[idx % len(work)]
+        with torch.cuda.stream(ws):
+            ci, v = pl.numeric(a_vals, b_vals)
+        done = torch.cuda.Event()
+        done.record(ws)
+        copy.wait_event(done)
+        with torch.cuda.stream(copy):
+            h_rp[rb:re].copy_(pl.row_ptr[:re - rb], non_blocking=True)
+            if n:
+                h_ci[o:o + n].copy_(ci, non_blocking=True)
+                h_v[o:o + n].copy_(v, non_blocking=True)
+        for t in (ci, v, pl.row_ptr):
+            t.record_stream(copy)
+    copy.synchronize()
+    rp = h_rp.numpy()
+    for idx, (rb, re) in enumerate(ranges):
+        if offs[idx]:
+            rp[rb:re] += np.int32(offs[idx])
+    rp[m] = total
+    for pl in plans:
+        pl.close()
+    base.close()
+    return h_rp[:m + 1], h_ci[:total], h_v[:total]
 
 
 def transpose(M: DeviceCSR, want_src: bool = False, dtype=None, stream=None):

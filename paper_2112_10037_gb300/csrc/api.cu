@@ -114,8 +114,10 @@ int numeric_window(const spgemm_opts& o) {
   return (o.window_warp == 2048 || o.window_warp == 4096) ? o.window_warp : 1024;
 }
 
+// own_b: the plan builds its own window-run lists of B (false: it reads
+// another plan's).
 Layout layout_for(const spgemm_opts& o, long long mloc, long long nnz_a, long long nrows_b, long long ncols_b,
-                  long long nnz_b) {
+                  long long nnz_b, bool own_b = true) {
   sg::SplitInfo sp;
   size_t nh = 0;
   split_geometry(o, numeric_window(o), mloc, ncols_b, &sp, &nh);
@@ -129,12 +131,15 @@ Layout layout_for(const spgemm_opts& o, long long mloc, long long nnz_a, long lo
   L.cursor = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
   L.nxt = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
   L.scan = off; off = align_up(off + sizeof(long long) * sg::scan_partials_count(mloc));
-  L.rr = off; off = align_up(off + sizeof(int32_t) * (size_t)(nrows_b + 1));
-  L.runs = off; off = align_up(off + sizeof(int2) * (size_t)(nnz_b + nrows_b + sg::RUNS_PAD));
-  L.runs_part = off; off = align_up(off + sizeof(long long) * sg::scan_partials_count(nrows_b));
+  L.rr = L.runs = L.runs_part = 0;
+  if (own_b) {
+    L.rr = off; off = align_up(off + sizeof(int32_t) * (size_t)(nrows_b + 1));
+    L.runs = off; off = align_up(off + sizeof(int2) * (size_t)(nnz_b + nrows_b + sg::RUNS_PAD));
+    L.runs_part = off; off = align_up(off + sizeof(long long) * sg::scan_partials_count(nrows_b));
+  }
   L.hcnt = off; off = align_up(off + sizeof(int32_t) * nh);
   L.rrb = L.runsb = 0;
-  if (numeric_block_bin(o) < sg::NBINS) {  // run list at the block window's width
+  if (own_b && numeric_block_bin(o) < sg::NBINS) {  // run list at the block window's width
     L.rrb = off; off = align_up(off + sizeof(int32_t) * (size_t)(nrows_b + 1));
     L.runsb = off; off = align_up(off + sizeof(int2) * (size_t)(nnz_b + nrows_b + sg::RUNS_PAD));
   }
@@ -255,6 +260,91 @@ spgemm_status read_stats(spgemm_plan* p, cudaStream_t s) {
 
 }  // namespace
 
+// base: another plan of the same product whose window-run lists of B this
+// plan reads instead of building its own (null: build them).
+static spgemm_status analyse_impl(const spgemm_csr* A, const spgemm_csr* B, const spgemm_opts* opts,
+                                  void* workspace, size_t workspace_bytes, spgemm_stream_t stream,
+                                  const spgemm_plan* base, spgemm_plan** plan) {
+  if (!plan) return SPGEMM_ERR_INVALID_ARG;
+  *plan = nullptr;
+  spgemm_status s;
+  if ((s = check_csr(A)) != SPGEMM_OK) return s;
+  if ((s = check_csr(B)) != SPGEMM_OK) return s;
+  if (A->ncols != B->nrows) return SPGEMM_ERR_DIM_MISMATCH;
+  spgemm_opts o;
+  if (opts) o = *opts; else spgemm_opts_default(&o);
+  if (o.dtype != SPGEMM_F64 && o.dtype != SPGEMM_F32) return SPGEMM_ERR_INVALID_ARG;
+  if (o.force_path < -1 || o.force_path > 4) return SPGEMM_ERR_INVALID_ARG;
+  const long long rb = o.row_begin, re = o.row_end < 0 ? A->nrows : o.row_end;
+  if (rb < 0 || re < rb || re > A->nrows) return SPGEMM_ERR_DIM_MISMATCH;
+  const Layout L = layout_for(o, re - rb, A->nnz, B->nrows, B->ncols, B->nnz, base == nullptr);
+  if (!workspace || workspace_bytes < L.total) return SPGEMM_ERR_WORKSPACE;
+  if (((uintptr_t)workspace) % 16) return SPGEMM_ERR_WORKSPACE;
+
+  spgemm_plan* p = new (std::nothrow) spgemm_plan();
+  if (!p) return SPGEMM_ERR_INTERNAL;
+  if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return SPGEMM_ERR_CUDA; }
+  p->nsm = sm_count_for(p->device);
+  if (p->nsm <= 0) { delete p; return SPGEMM_ERR_CUDA; }
+  p->A = sg::Csr{A->row_ptr, A->col_idx, A->nrows, A->ncols, A->nnz};
+  p->B = sg::Csr{B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz};
+  p->opts = o;
+  p->row_begin = rb;
+  p->mloc = re - rb;
+  p->ws = (unsigned char*)workspace;
+  p->ws_bytes = workspace_bytes;
+  p->st = (sg::DevStats*)(p->ws + L.st);
+  p->prod = (long long*)(p->ws + L.prod);
+  p->cmin = (int*)(p->ws + L.cmin);
+  p->cmax = (int*)(p->ws + L.cmax);
+  p->rows = (int*)(p->ws + L.rows);
+  p->cursor = (int32_t*)(p->ws + L.cursor);
+  p->nxt = (int32_t*)(p->ws + L.nxt);
+  p->scan_part = (long long*)(p->ws + L.scan);
+  choose_paths(o, &p->pb, &p->tu);
+  {
+    size_t nh = 0;
+    split_geometry(o, p->tu.window_warp, p->mloc, B->ncols, &p->sp, &nh);
+    p->sp.hcnt = nh ? (int32_t*)(p->ws + L.hcnt) : nullptr;
+    p->sp.wb_shift = 0;
+    while ((1 << p->sp.wb_shift) < p->tu.window_block) ++p->sp.wb_shift;
+    if (base) {
+      p->sp.rr = base->sp.rr;
+      p->sp.runs = base->sp.runs;
+      p->sp.rrb = base->sp.rrb;
+      p->sp.runsb = base->sp.runsb;
+      p->runs_part = nullptr;
+    } else {
+      p->sp.rr = (int32_t*)(p->ws + L.rr);
+      p->sp.runs = (int2*)(p->ws + L.runs);
+      p->sp.rrb = L.rrb ? (int32_t*)(p->ws + L.rrb) : nullptr;
+      p->sp.runsb = L.runsb ? (int2*)(p->ws + L.runsb) : nullptr;
+      p->runs_part = (long long*)(p->ws + L.runs_part);
+    }
+  }
+
+  cudaStream_t st = (cudaStream_t)stream;
+  sg::LaunchCtx c = ctx_of(p, stream);
+  cudaError_t e = cudaMemsetAsync(p->st, 0, sizeof(sg::DevStats), st);
+  if (e == cudaSuccess && o.validate) {
+    e = sg::launch_validate(c, p->A);
+    if (e == cudaSuccess) e = sg::launch_validate(c, p->B);
+  }
+  if (e == cudaSuccess) e = sg::launch_analyse(c, p->A, p->B, p->row_begin, p->mloc, p->prod, p->cmin, p->cmax, p->rows);
+  if (e == cudaSuccess && !base) e = sg::launch_runs(c, p->B, p->sp, p->runs_part);
+  if (e == cudaSuccess && o.backward) {
+    p->at_rp = (int32_t*)(p->ws + L.at_rp);
+    p->at_ci = (int32_t*)(p->ws + L.at_ci);
+    p->at_src = (int32_t*)(p->ws + L.at_src);
+    int32_t* tmp = (int32_t*)(p->ws + L.at_tmp);
+    e = sg::launch_transpose(c, A->nrows, A->ncols, A->nnz, A->row_ptr, A->col_idx, p->at_rp, p->at_ci, p->at_src,
+                             (int32_t*)(p->ws + L.at_fill), tmp, tmp + A->nnz, (long long*)(p->ws + L.at_part));
+  }
+  if (e != cudaSuccess) { delete p; return SPGEMM_ERR_CUDA; }
+  *plan = p;
+  return SPGEMM_OK;
+}
+
 extern "C" {
 
 void spgemm_opts_default(spgemm_opts* o) {
@@ -310,76 +400,44 @@ spgemm_status spgemm_workspace_size(const spgemm_csr* A, const spgemm_csr* B, co
 spgemm_status spgemm_analyse(const spgemm_csr* A, const spgemm_csr* B, const spgemm_opts* opts,
                              void* workspace, size_t workspace_bytes, spgemm_stream_t stream,
                              spgemm_plan** plan) {
+  return analyse_impl(A, B, opts, workspace, workspace_bytes, stream, nullptr, plan);
+}
+
+// Options, A and B of a row-range plan derived from base.
+static void rows_args(const spgemm_plan* base, int64_t rb, int64_t re, spgemm_csr* A, spgemm_csr* B,
+                      spgemm_opts* o) {
+  *A = spgemm_csr{base->A.nrows, base->A.ncols, base->A.nnz, base->A.rp, base->A.ci, nullptr};
+  *B = spgemm_csr{base->B.nrows, base->B.ncols, base->B.nnz, base->B.rp, base->B.ci, nullptr};
+  *o = base->opts;
+  o->row_begin = rb;
+  o->row_end = re;
+  o->backward = 0;
+  o->validate = 0;
+}
+
+spgemm_status spgemm_rows_workspace_size(const spgemm_plan* base, int64_t row_begin, int64_t row_end,
+                                         size_t* bytes) {
+  if (!base || !bytes) return SPGEMM_ERR_INVALID_ARG;
+  if (!base->sp.rr || !base->sp.runs) return SPGEMM_ERR_NOT_READY;
+  if (row_begin < 0 || row_end < row_begin || row_end > base->A.nrows) return SPGEMM_ERR_DIM_MISMATCH;
+  spgemm_csr A, B;
+  spgemm_opts o;
+  rows_args(base, row_begin, row_end, &A, &B, &o);
+  *bytes = layout_for(o, row_end - row_begin, A.nnz, B.nrows, B.ncols, B.nnz, false).total;
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_analyse_rows(const spgemm_plan* base, int64_t row_begin, int64_t row_end, void* workspace,
+                                  size_t workspace_bytes, spgemm_stream_t stream, spgemm_plan** plan) {
   if (!plan) return SPGEMM_ERR_INVALID_ARG;
   *plan = nullptr;
-  spgemm_status s;
-  if ((s = check_csr(A)) != SPGEMM_OK) return s;
-  if ((s = check_csr(B)) != SPGEMM_OK) return s;
-  if (A->ncols != B->nrows) return SPGEMM_ERR_DIM_MISMATCH;
+  if (!base) return SPGEMM_ERR_INVALID_ARG;
+  if (!base->sp.rr || !base->sp.runs) return SPGEMM_ERR_NOT_READY;
+  if (row_begin < 0 || row_end < row_begin || row_end > base->A.nrows) return SPGEMM_ERR_DIM_MISMATCH;
+  spgemm_csr A, B;
   spgemm_opts o;
-  if (opts) o = *opts; else spgemm_opts_default(&o);
-  if (o.dtype != SPGEMM_F64 && o.dtype != SPGEMM_F32) return SPGEMM_ERR_INVALID_ARG;
-  if (o.force_path < -1 || o.force_path > 4) return SPGEMM_ERR_INVALID_ARG;
-  const long long rb = o.row_begin, re = o.row_end < 0 ? A->nrows : o.row_end;
-  if (rb < 0 || re < rb || re > A->nrows) return SPGEMM_ERR_DIM_MISMATCH;
-  const Layout L = layout_for(o, re - rb, A->nnz, B->nrows, B->ncols, B->nnz);
-  if (!workspace || workspace_bytes < L.total) return SPGEMM_ERR_WORKSPACE;
-  if (((uintptr_t)workspace) % 16) return SPGEMM_ERR_WORKSPACE;
-
-  spgemm_plan* p = new (std::nothrow) spgemm_plan();
-  if (!p) return SPGEMM_ERR_INTERNAL;
-  if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return SPGEMM_ERR_CUDA; }
-  p->nsm = sm_count_for(p->device);
-  if (p->nsm <= 0) { delete p; return SPGEMM_ERR_CUDA; }
-  p->A = sg::Csr{A->row_ptr, A->col_idx, A->nrows, A->ncols, A->nnz};
-  p->B = sg::Csr{B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz};
-  p->opts = o;
-  p->row_begin = rb;
-  p->mloc = re - rb;
-  p->ws = (unsigned char*)workspace;
-  p->ws_bytes = workspace_bytes;
-  p->st = (sg::DevStats*)(p->ws + L.st);
-  p->prod = (long long*)(p->ws + L.prod);
-  p->cmin = (int*)(p->ws + L.cmin);
-  p->cmax = (int*)(p->ws + L.cmax);
-  p->rows = (int*)(p->ws + L.rows);
-  p->cursor = (int32_t*)(p->ws + L.cursor);
-  p->nxt = (int32_t*)(p->ws + L.nxt);
-  p->scan_part = (long long*)(p->ws + L.scan);
-  choose_paths(o, &p->pb, &p->tu);
-  {
-    size_t nh = 0;
-    split_geometry(o, p->tu.window_warp, p->mloc, B->ncols, &p->sp, &nh);
-    p->sp.rr = (int32_t*)(p->ws + L.rr);
-    p->sp.runs = (int2*)(p->ws + L.runs);
-    p->sp.hcnt = nh ? (int32_t*)(p->ws + L.hcnt) : nullptr;
-    p->sp.wb_shift = 0;
-    while ((1 << p->sp.wb_shift) < p->tu.window_block) ++p->sp.wb_shift;
-    p->sp.rrb = L.rrb ? (int32_t*)(p->ws + L.rrb) : nullptr;
-    p->sp.runsb = L.runsb ? (int2*)(p->ws + L.runsb) : nullptr;
-    p->runs_part = (long long*)(p->ws + L.runs_part);
-  }
-
-  cudaStream_t st = (cudaStream_t)stream;
-  sg::LaunchCtx c = ctx_of(p, stream);
-  cudaError_t e = cudaMemsetAsync(p->st, 0, sizeof(sg::DevStats), st);
-  if (e == cudaSuccess && o.validate) {
-    e = sg::launch_validate(c, p->A);
-    if (e == cudaSuccess) e = sg::launch_validate(c, p->B);
-  }
-  if (e == cudaSuccess) e = sg::launch_analyse(c, p->A, p->B, p->row_begin, p->mloc, p->prod, p->cmin, p->cmax, p->rows);
-  if (e == cudaSuccess) e = sg::launch_runs(c, p->B, p->sp, p->runs_part);
-  if (e == cudaSuccess && o.backward) {
-    p->at_rp = (int32_t*)(p->ws + L.at_rp);
-    p->at_ci = (int32_t*)(p->ws + L.at_ci);
-    p->at_src = (int32_t*)(p->ws + L.at_src);
-    int32_t* tmp = (int32_t*)(p->ws + L.at_tmp);
-    e = sg::launch_transpose(c, A->nrows, A->ncols, A->nnz, A->row_ptr, A->col_idx, p->at_rp, p->at_ci, p->at_src,
-                             (int32_t*)(p->ws + L.at_fill), tmp, tmp + A->nnz, (long long*)(p->ws + L.at_part));
-  }
-  if (e != cudaSuccess) { delete p; return SPGEMM_ERR_CUDA; }
-  *plan = p;
-  return SPGEMM_OK;
+  rows_args(base, row_begin, row_end, &A, &B, &o);
+  return analyse_impl(&A, &B, &o, workspace, workspace_bytes, stream, base, plan);
 }
 
 spgemm_status spgemm_symbolic(spgemm_plan* p, int32_t* c_row_ptr, int64_t* c_nnz, spgemm_stream_t stream) {
