@@ -378,7 +378,7 @@ def run_e2e(args, api, torch, dev, A, B, kw, products):
         dA = api.DeviceCSR(A.nrows, A.ncols, d_rp, d_ci, d_v)
         dB = dA if B is A else api.DeviceCSR.from_host(B, device=dev)
         rp, ci, v = api.spgemm_to_host(dA, dB, dtype=torch.float64, chunks=args.e2e_chunks,
-                                       streams=args.e2e_streams, out=out, **kw)
+                                       streams=args.e2e_streams, out=out, order=args.e2e_order, **kw)
         return (rp, ci, v), ci.numel(), rp.numel()
 
     out, nnz, nrp = once()
@@ -624,6 +624,8 @@ def main():
     ap.add_argument("--e2e-chunks", type=int, default=4,
                     help="row ranges of the end-to-end leg (computed while earlier ranges are copied back)")
     ap.add_argument("--e2e-streams", type=int, default=1, help="compute streams of the end-to-end leg")
+    ap.add_argument("--e2e-order", default="rows", choices=["products", "rows"],
+                    help="order of the end-to-end leg's row ranges")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -185,7 +185,7 @@ def _stream_pool(dev, name, n):
 
 
 def spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int = 4, streams: int = 1, out=None,
-                   **opt_kw):
+                   order: str = "rows", **opt_kw):
     """C = A*B with C delivered in pinned host memory.
 
     Rows of C are independent (Sec. 2.2), so C is computed in ``chunks`` row
@@ -197,7 +197,9 @@ def spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int 
     and the last range's copy are not hidden.  Each range waits for its own
     longest rows, which one whole-matrix pass would overlap with other work,
     so a few ranges (default 4, one compute stream) do best on power-law
-    matrices.  ``out`` = (row_ptr, col_idx, vals) pinned CPU tensors
+    matrices.  ``order="products"`` computes the lightest range first, the
+    second lightest last and the others heaviest first (``"rows"``: row
+    order).  ``out`` = (row_ptr, col_idx, vals) pinned CPU tensors
     to fill, reused when large enough.  Returns CPU tensors (row_ptr,
     col_idx, vals); blocks until they are complete."""
     dev = A.row_ptr.device
@@ -232,7 +234,15 @@ def spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int 
                torch.empty(max(total, 1), dtype=torch.int32).pin_memory(),
                torch.empty(max(total, 1), dtype=dtype).pin_memory())
     h_rp, h_ci, h_v = out
-    for idx in range(len(plans)):
+    if order == "products" and len(plans) > 2:
+        # the range computed first and the range copied last are not hidden:
+        # make them the two lightest, heavy ranges in between
+        prods = [pl.stats()[0] for pl in plans]
+        by = sorted(range(len(plans)), key=lambda i: prods[i])
+        seq = [by[0]] + sorted(by[2:], key=lambda i: -prods[i]) + [by[1]]
+    else:
+        seq = list(range(len(plans)))
+    for idx in seq:
         pl, (rb, re) = plans[idx], ranges[idx]
         o, n = int(offs[idx]), nnzs[idx]
         ws = work[idx % len(work)]
