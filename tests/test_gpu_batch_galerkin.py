@@ -131,3 +131,7 @@ def test_galerkin_96_matches_two_plain_calls(api, oracle_mod):
     assert_structure_equal(Ac, plain)
     assert_values_exact(Ac.vals, plain.vals)
     assert g.AP.nnz == 3483648
+    # and against the oracle at this full size (integer values: exact)
+    ref = oracle_mod.spgemm(oracle_mod.transpose(P), oracle_mod.spgemm(A, P))
+    assert_structure_equal(Ac, ref)
+    assert_values_exact(Ac.vals, ref.vals)

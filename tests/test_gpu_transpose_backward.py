@@ -143,3 +143,39 @@ def test_backward_fp32_vs_fp64_oracle(api, oracle_mod):
     sa, sb = _scale_sums(oracle_mod, A32, B32, C, W)
     assert max_rel_err(a.grad.double().cpu().numpy(), rda, sa) <= RTOL_F32
     assert max_rel_err(b.grad.double().cpu().numpy(), rdb, sb) <= RTOL_F32
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_backward_full_size_65536(api, oracle_mod, dtype):
+    """The differentiation workload at full size (A, B 65536^2, 32 random
+    columns per row, the bench's seeds): forward C and both gradients against
+    the FP64 oracle."""
+    n = 65536
+    A = gen.random_rows(n, n, np.full(n, 32), np.random.default_rng(0))
+    B = gen.random_rows(n, n, np.full(n, 32), np.random.default_rng(1))
+    dA, dB = api.DeviceCSR.from_host(A, dtype=dtype), api.DeviceCSR.from_host(B, dtype=dtype)
+    plan = api.Plan(dA, dB, dtype=dtype, backward=True)
+    rp, nnz = plan.symbolic()
+    ci, v = plan.numeric(dA.vals, dB.vals)
+    W = np.random.default_rng(2).standard_normal(nnz)
+    da, db = plan.backward(dA.vals, dB.vals, torch.from_numpy(W).to(device="cuda", dtype=dtype))
+    torch.cuda.synchronize()
+    plan.check()
+    Wq = W.astype(np.float32).astype(np.float64) if dtype == torch.float32 else W
+    Aq = A if dtype == torch.float64 else gen.CSR(A.nrows, A.ncols, A.row_ptr, A.col_idx,
+                                                  A.vals.astype(np.float32).astype(np.float64))
+    Bq = B if dtype == torch.float64 else gen.CSR(B.nrows, B.ncols, B.row_ptr, B.col_idx,
+                                                  B.vals.astype(np.float32).astype(np.float64))
+    C, rda, rdb = _grad_oracle(oracle_mod, Aq, Bq, Wq)
+    assert nnz == C.nnz
+    assert np.array_equal(rp.cpu().numpy().astype(np.int64), C.row_ptr.astype(np.int64))
+    assert np.array_equal(ci.cpu().numpy(), C.col_idx)
+    sa, sb = _scale_sums(oracle_mod, Aq, Bq, C, Wq)
+    tol = 1e-12 if dtype == torch.float64 else RTOL_F32
+    from parity import abs_csr
+    S = oracle_mod.spgemm(abs_csr(Aq), abs_csr(Bq))
+    assert max_rel_err(v.double().cpu().numpy(), C.vals, S.vals) <= tol
+    assert max_rel_err(da.double().cpu().numpy(), rda, sa) <= tol
+    assert max_rel_err(db.double().cpu().numpy(), rdb, sb) <= tol
+    plan.close()
