@@ -98,7 +98,9 @@ typedef struct spgemm_opts {
                           with a block-wide window (0: default 32768; -1: never, then
                           heavy rows are split as split_min says) */
   int32_t block_warps; /* warps sharing a numeric block window (see window_block) */
-  int32_t reserved[3];
+  int32_t sort_max;    /* rows of at most this many products are merged by a sort in
+                          registers: 128, 256 or 512 (0: 128) */
+  int32_t reserved[2];
 } spgemm_opts;
 
 typedef struct spgemm_plan spgemm_plan;

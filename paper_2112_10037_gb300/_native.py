@@ -44,7 +44,8 @@ class spgemm_opts(ctypes.Structure):
                 ("hash_max", ctypes.c_int32), ("window_warp", ctypes.c_int32),
                 ("window_block", ctypes.c_int32), ("split_min", ctypes.c_int32),
                 ("backward", ctypes.c_int32), ("num_block_min", ctypes.c_int32),
-                ("block_warps", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("block_warps", ctypes.c_int32), ("sort_max", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 _lib = None

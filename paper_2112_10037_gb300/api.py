@@ -63,7 +63,7 @@ def _stream_handle(stream=None) -> int:
 
 def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1, warp_max=0,
               window_warp=0, window_block=0, split_min=0, backward=False, num_block_min=0,
-              block_warps=0) -> nat.spgemm_opts:
+              block_warps=0, sort_max=0) -> nat.spgemm_opts:
     o = nat.spgemm_opts_default()
     o.dtype = _DT[dtype]
     o.validate = 1 if validate else 0
@@ -77,6 +77,7 @@ def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1
     o.backward = 1 if backward else 0
     o.num_block_min = int(num_block_min)
     o.block_warps = int(block_warps)
+    o.sort_max = int(sort_max)
     return o
 
 

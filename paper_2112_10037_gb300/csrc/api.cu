@@ -71,6 +71,13 @@ size_t transpose_layout(size_t off, long long n, long long nnz, size_t* fill, si
 
 int numeric_block_bin(const spgemm_opts& o);
 
+// Last bin of the register-sort path: rows of at most 128, 256 or 512
+// products (opts.sort_max; bin b holds products in (2^(b-2), 2^(b-1)]).
+int tiny_hi_bin(const spgemm_opts& o) {
+  const int m = o.sort_max > 0 ? o.sort_max : 128;
+  return m >= 512 ? 10 : (m >= 256 ? 9 : 8);
+}
+
 // Window geometry and split capacity from the options and B's width (see
 // sg::SplitInfo).  *hcnt_entries is 0 when no row is split.
 void split_geometry(const spgemm_opts& o, int window, long long mloc, long long ncols_b, sg::SplitInfo* sp,
@@ -93,7 +100,7 @@ void split_geometry(const spgemm_opts& o, int window, long long mloc, long long 
   // split rows always lie above the register-sort bins (1..8), so their
   // sizes come from the bitmap-window kernel, which records per-window counts
   sp->heavy_bin = sg::bin_of(smin) + 1;
-  if (sp->heavy_bin < 9) sp->heavy_bin = 9;
+  if (sp->heavy_bin < tiny_hi_bin(o) + 1) sp->heavy_bin = tiny_hi_bin(o) + 1;
   if (sp->heavy_bin >= sg::NBINS) { sp->heavy_bin = sg::NBINS; return; }
   sp->hcap = (int)cap;
   *hcnt_entries = (size_t)cap * (size_t)sp->ntf;
@@ -102,12 +109,12 @@ void split_geometry(const spgemm_opts& o, int window, long long mloc, long long 
 // First bin of rows whose numeric pass uses the block-wide window.
 int numeric_block_bin(const spgemm_opts& o) {
   if (o.force_path == 1 || o.force_path == 3) return sg::NBINS;  // warp window only
-  if (o.force_path == 2) return 9;                                 // every row above the register sort
+  if (o.force_path == 2) return tiny_hi_bin(o) + 1;                 // every row above the register sort
   if (o.force_path == 4) return 1;                                 // every non-empty row
   if (o.num_block_min < 0) return sg::NBINS;
   const long long m = o.num_block_min > 0 ? o.num_block_min : 32768;
   const int b = sg::bin_of(m) + 1;
-  return b < 9 ? 9 : b;
+  return b < tiny_hi_bin(o) + 1 ? tiny_hi_bin(o) + 1 : b;
 }
 
 int numeric_window(const spgemm_opts& o) {
@@ -199,7 +206,7 @@ void choose_paths(const spgemm_opts& o, sg::PathBins* pb, sg::Tuning* tu) {
   block_geometry(o, &tu->window_block, &tu->block_warps);
   tu->hash_max = 0;
   tu->num_lo_block = numeric_block_bin(o);
-  constexpr int TINY_HI = 8;  // register sort up to 128 products
+  const int TINY_HI = tiny_hi_bin(o);  // register sort up to opts.sort_max products
   const int wb = sg::bin_of(tu->warp_max) < TINY_HI + 1 ? TINY_HI + 1 : sg::bin_of(tu->warp_max);
   for (int p = 0; p < sg::NPATHS; ++p) { pb->lo[p] = 1; pb->hi[p] = 0; }
   switch (o.force_path) {

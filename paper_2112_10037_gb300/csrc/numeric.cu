@@ -68,8 +68,9 @@ static cudaError_t block_num(const LaunchCtx& c, const Csr& A, const Csr& B, con
   return cudaGetLastError();
 }
 
-template <typename F8, typename F16, typename F32, typename F64, typename F128>
-static cudaError_t tiny_dispatch(int lo, int hi, F8 f8, F16 f16, F32 f32, F64 f64, F128 f128) {
+template <typename F8, typename F16, typename F32, typename F64, typename F128, typename F256, typename F512>
+static cudaError_t tiny_dispatch(int lo, int hi, F8 f8, F16 f16, F32 f32, F64 f64, F128 f128, F256 f256,
+                                 F512 f512) {
   cudaError_t e = cudaSuccess;
   auto clip = [&](int a, int b, auto f) -> cudaError_t {
     const int l = lo > a ? lo : a, h = hi < b ? hi : b;
@@ -80,6 +81,8 @@ static cudaError_t tiny_dispatch(int lo, int hi, F8 f8, F16 f16, F32 f32, F64 f6
   if ((e = clip(6, 6, f32))) return e;
   if ((e = clip(7, 7, f64))) return e;
   if ((e = clip(8, 8, f128))) return e;
+  if ((e = clip(9, 9, f256))) return e;
+  if ((e = clip(10, 10, f512))) return e;
   return cudaSuccess;
 }
 
@@ -97,7 +100,9 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
         [&](int l, int h) { return tiny_num<T, 16, 1>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
         [&](int l, int h) { return tiny_num<T, 32, 1>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
         [&](int l, int h) { return tiny_num<T, 32, 2>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
-        [&](int l, int h) { return tiny_num<T, 32, 4>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); });
+        [&](int l, int h) { return tiny_num<T, 32, 4>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
+        [&](int l, int h) { return tiny_num<T, 32, 8>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
+        [&](int l, int h) { return tiny_num<T, 32, 16>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); });
     timer_mark(c, T_NUM_TINY, 1);
     if (e) return e;
   }

@@ -27,9 +27,10 @@ static cudaError_t tiny_sym(const LaunchCtx& c, const Csr& A, const Csr& B, cons
 }
 
 // Register-sort bins: 1..4 -> 8 lanes, 5 -> 16 lanes, 6 -> 32 lanes,
-// 7 -> 32 lanes x 2 slots, 8 -> 32 lanes x 4 slots (P <= 128).
-template <typename F8, typename F16, typename F32, typename F64, typename F128>
-static cudaError_t tiny_dispatch(int lo, int hi, F8 f8, F16 f16, F32 f32, F64 f64, F128 f128) {
+// 7 -> 32 lanes x 2 slots, 8 -> x 4, 9 -> x 8, 10 -> x 16 slots (P <= 512).
+template <typename F8, typename F16, typename F32, typename F64, typename F128, typename F256, typename F512>
+static cudaError_t tiny_dispatch(int lo, int hi, F8 f8, F16 f16, F32 f32, F64 f64, F128 f128, F256 f256,
+                                 F512 f512) {
   cudaError_t e = cudaSuccess;
   auto clip = [&](int a, int b, auto f) -> cudaError_t {
     const int l = lo > a ? lo : a, h = hi < b ? hi : b;
@@ -40,6 +41,8 @@ static cudaError_t tiny_dispatch(int lo, int hi, F8 f8, F16 f16, F32 f32, F64 f6
   if ((e = clip(6, 6, f32))) return e;
   if ((e = clip(7, 7, f64))) return e;
   if ((e = clip(8, 8, f128))) return e;
+  if ((e = clip(9, 9, f256))) return e;
+  if ((e = clip(10, 10, f512))) return e;
   return cudaSuccess;
 }
 
@@ -84,7 +87,9 @@ cudaError_t launch_symbolic(const LaunchCtx& c, const Csr& A, const Csr& B, cons
         [&](int l, int h) { return tiny_sym<16, 1>(c, A, B, ri, l, h, c_cnt, rows); },
         [&](int l, int h) { return tiny_sym<32, 1>(c, A, B, ri, l, h, c_cnt, rows); },
         [&](int l, int h) { return tiny_sym<32, 2>(c, A, B, ri, l, h, c_cnt, rows); },
-        [&](int l, int h) { return tiny_sym<32, 4>(c, A, B, ri, l, h, c_cnt, rows); });
+        [&](int l, int h) { return tiny_sym<32, 4>(c, A, B, ri, l, h, c_cnt, rows); },
+        [&](int l, int h) { return tiny_sym<32, 8>(c, A, B, ri, l, h, c_cnt, rows); },
+        [&](int l, int h) { return tiny_sym<32, 16>(c, A, B, ri, l, h, c_cnt, rows); });
     timer_mark(c, T_SYM_TINY, 1);
     if (e) return e;
   }

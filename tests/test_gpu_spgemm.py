@@ -95,7 +95,7 @@ def test_wide_rows_many_windows(api, oracle_mod, force):
     assert_values_close(C.vals, R.vals, S)
 
 
-@pytest.mark.parametrize("P", [1, 7, 8, 9, 15, 16, 17, 31, 32, 33, 64, 65])
+@pytest.mark.parametrize("P", [1, 7, 8, 9, 15, 16, 17, 31, 32, 33, 64, 65, 128, 129, 256, 257, 512, 513])
 def test_bin_boundaries(api, oracle_mod, P):
     """Rows whose product count sits on each side of a bin edge."""
     rng = np.random.default_rng(P)
@@ -262,14 +262,15 @@ def test_many_nonzeros_per_row_global_cursors(api, oracle_mod):
     assert_values_close(C.vals, R.vals, S)
 
 
-@pytest.mark.parametrize("P", [65, 96, 127, 128, 129])
-def test_register_sort_multi_slot(api, oracle_mod, P):
+@pytest.mark.parametrize("sort_max", [128, 256, 512])
+@pytest.mark.parametrize("P", [65, 96, 127, 128, 129, 200, 256, 257, 400, 512, 513])
+def test_register_sort_multi_slot(api, oracle_mod, P, sort_max):
     rng = np.random.default_rng(P)
     B = gen.random_rows(P, 200, np.ones(P, np.int64), rng, values="int")
     A = gen.CSR(2, P, np.array([0, P, 2 * P], np.int32),
                 np.concatenate([np.arange(P), np.arange(P)]).astype(np.int32),
                 np.ones(2 * P))
-    C, _ = run(api, A, B)
+    C, _ = run(api, A, B, sort_max=sort_max)
     R = oracle_mod.spgemm(A, B)
     assert_structure_equal(C, R)
     assert_values_exact(C.vals, R.vals)
