@@ -40,10 +40,10 @@ template <int W, int NW, typename T>
 __host__ __device__ constexpr size_t numblock_smem_bytes() {
   return (size_t)W * sizeof(T)                 // window values
          + (size_t)nb_segcap<NW>() * sizeof(T)  // segment multipliers A(i,k)
-         + (size_t)(W / 32) * 4                // presence bitmap
+         + (size_t)(W / 32) * 8                // two presence bitmaps (alternate windows)
          + (size_t)nb_segcap<NW>() * 8         // segment stream offsets and starts in B
          + (size_t)NW * 8                      // per-warp counts and next windows
-         + (size_t)(W / 32) * 4;               // per-word output offsets inside a warp's share
+         + (size_t)(W / 32) * 2;               // per-word output offsets inside a warp's share
 }
 
 // Loads of one step of U batches of 32 products from pb on: column, B value
@@ -140,7 +140,7 @@ __device__ __forceinline__ void nb_range(const Csr& B, const T* __restrict__ bv,
 // offsets, its word from a binary search over the chunk's offsets, its bit
 // from a binary search on popcounts inside the word.  Every lane must call it.
 template <int NW, int WPW, typename T>
-__device__ __forceinline__ void nb_emit(const uint32_t* bits, const int* wpre, const int* wcnt, T* acc, int base,
+__device__ __forceinline__ void nb_emit(const uint32_t* bits, const uint16_t* wpre, const int* wcnt, T* acc, int base,
                                         int out, int out_end, int32_t* __restrict__ rci, T* __restrict__ rcv,
                                         uint32_t* err) {
   const int lane = lane_id(), warp = threadIdx.x >> 5;
@@ -155,7 +155,7 @@ __device__ __forceinline__ void nb_emit(const uint32_t* bits, const int* wpre, c
     const int coff = __shfl_sync(FULL, cinc - cnt, c & 31);
     if (t < hi) {
       const int rel = t - coff;
-      const int* pre = wpre + c * WPW;
+      const uint16_t* pre = wpre + c * WPW;
       int wj = 0;  // last word of the chunk whose offset is <= rel
 #pragma unroll
       for (int sh = 16; sh >= 1; sh >>= 1)
@@ -206,19 +206,22 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* acc = reinterpret_cast<T*>(smem_raw);
   T* seg_a = acc + W;
-  uint32_t* bits = reinterpret_cast<uint32_t*>(seg_a + SEGCAP);
-  int* seg_off = reinterpret_cast<int*>(bits + NWORDS);
+  // presence bitmaps of alternate windows: a window's bitmap is cleared
+  // during the next window, so the emission needs no closing barrier
+  uint32_t* bits0 = reinterpret_cast<uint32_t*>(seg_a + SEGCAP);
+  uint32_t* bits1 = bits0 + NWORDS;
+  int* seg_off = reinterpret_cast<int*>(bits1 + NWORDS);
   int* seg_s = seg_off + SEGCAP;
   int* wcnt = seg_s + SEGCAP;
   int* wnext = wcnt + NW;
-  int* wpre = wnext + NW;
+  uint16_t* wpre = reinterpret_cast<uint16_t*>(wnext + NW);  // word offsets inside a chunk (< 1024)
   __shared__ int s_lb, s_le, s_item;
   // (segments << 32) | products collected so far in a round; two of them, so
   // one can be cleared while the other is read
   __shared__ unsigned long long s_pack[2];
   const int warp = threadIdx.x >> 5, lane = lane_id();
   for (int t = threadIdx.x; t < W; t += NW * 32) acc[t] = T(0);
-  for (int t = threadIdx.x; t < NWORDS; t += NW * 32) bits[t] = 0u;
+  for (int t = threadIdx.x; t < 2 * NWORDS; t += NW * 32) bits0[t] = 0u;
   if (threadIdx.x == 0) {
     bin_range(st, bin_lo, bin_hi, &s_lb, &s_le);
     s_pack[0] = 0ull;
@@ -227,6 +230,11 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
   if (block_skip(st)) return;
   const int lb = s_lb, le = s_le;
   int parity = 0;  // which s_pack the current round uses
+  int bsel = 0;    // bitmap of the current window
+  // this warp's non-empty words of the previous window's bitmap, cleared
+  // once every warp has finished that window's emission
+  uint32_t prev_w = 0u;
+  int prev_i = 0;
 
   while (true) {
     if (threadIdx.x == 0) s_item = (int)atomicAdd(counter, 1u);
@@ -276,7 +284,9 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
     int out = 0;
     while (wb != INT_MAX) {
       const int base = wb << WSHIFT;
+      uint32_t* const bits = bsel ? bits1 : bits0;
       mn = INT_MAX;
+      bool first_round = true;
       for (int r0 = a0; r0 < a1; r0 += SEGCAP) {  // one round with register cursors
         const int r1 = min(a1, r0 + SEGCAP);
         unsigned long long* pk = &s_pack[parity];
@@ -312,7 +322,12 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
             seg_append<T>(pk, s, len, a, seg_off, seg_s, seg_a);
           }
         }
-        __syncthreads();  // the list is complete
+        __syncthreads();  // the list is complete (and the previous window emitted)
+        if (first_round) {
+          if (prev_w) (bsel ? bits0 : bits1)[prev_i] = 0u;
+          prev_w = 0u;
+          first_round = false;
+        }
         const unsigned long long pv = *pk;
         const int nseg = (int)(pv >> 32), tot = (int)(unsigned)(pv & 0xffffffffull);
         if (threadIdx.x == 0) s_pack[parity ^ 1] = 0ull;  // for the next round
@@ -334,7 +349,7 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
       const uint32_t myw = (lane < WPW && wi < nwd) ? bits[wi] : 0u;
       const int c = __popc(myw);
       const int inc = warp_incl_scan(c);
-      if (lane < WPW) wpre[wi] = inc - c;
+      if (lane < WPW) wpre[wi] = (uint16_t)(inc - c);
       if (lane == 31) {
         wcnt[warp] = inc;
         wnext[warp] = mn;
@@ -347,8 +362,12 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
       }
       nb_emit<NW, WPW, T>(bits, wpre, wcnt, acc, base, out, out_end, rci, rcv, err);
       out += total;
-      __syncthreads();  // every warp is done reading bits, wpre and wcnt
-      if (myw) bits[wi] = 0u;
+      // no barrier: the next window's list barrier orders this emission
+      // before its products (which use the other bitmap, and find the
+      // emitted accumulator entries zeroed) and before this bitmap's clear
+      prev_w = myw;
+      prev_i = wi;
+      bsel ^= 1;
       wb = nb;
     }
     if (threadIdx.x == 0 && out != out_end) atomicOr(err, EB_INTERNAL);
