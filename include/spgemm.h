@@ -149,6 +149,18 @@ spgemm_status spgemm_analyse_rows(const spgemm_plan* base, int64_t row_begin, in
                                   void* workspace, size_t workspace_bytes,
                                   spgemm_stream_t stream, spgemm_plan** plan);
 
+/* Sizes a plan without its symbolic pass, from row sizes computed elsewhere
+ * (for a row-range plan: the whole product's symbolic pass).  The c_row_ptr
+ * later given to spgemm_numeric must then hold, for each of the plan's rows,
+ * the offset of the row's first entry in the caller's c_col_idx / c_vals
+ * (for example a slice of the whole product's row pointer, so that ranges are
+ * written in place), and nnz is the number of entries of the plan's rows.
+ * Rows whose sizes disagree with their products are written only inside
+ * their given extent and reported as SPGEMM_ERR_INTERNAL.  Plans with split
+ * rows (split_min) need the symbolic pass: SPGEMM_ERR_NOT_READY.  BLOCKS on
+ * `stream` to read the analysis results. */
+spgemm_status spgemm_plan_adopt_row_ptr(spgemm_plan* plan, int64_t nnz, spgemm_stream_t stream);
+
 /* Symbolic pass: sizes every row of C (the number of distinct columns the
  * row's products reach, Sec. 2.2) and writes C's row pointer to c_row_ptr
  * (device, int32, nrows(C)+1 entries) by an exclusive prefix sum.  BLOCKS on

@@ -66,6 +66,7 @@ _SIG = {
     "spgemm_analyse_rows": ([ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_size_t,
                              ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
     "spgemm_symbolic": ([_P, _P, _I64P, _P], ctypes.c_int),
+    "spgemm_plan_adopt_row_ptr": ([_P, ctypes.c_int64, _P], ctypes.c_int),
     "spgemm_numeric": ([_P, _P, _P, _P, _P, _P, _P], ctypes.c_int),
     "spgemm_plan_stats": ([_P, _P, _I64P, _I64P, _I64P], ctypes.c_int),
     "spgemm_plan_check": ([_P, _P], ctypes.c_int),
@@ -161,6 +162,10 @@ def spgemm_analyse_rows(base: int, row_begin: int, row_end: int, workspace: int,
                                      ctypes.c_size_t(workspace_bytes), _P(stream), ctypes.byref(plan)),
            "spgemm_analyse_rows")
     return plan.value
+
+
+def spgemm_plan_adopt_row_ptr(plan: int, nnz: int, stream: int) -> None:
+    _check(lib().spgemm_plan_adopt_row_ptr(_P(plan), ctypes.c_int64(nnz), _P(stream)), "spgemm_plan_adopt_row_ptr")
 
 
 def spgemm_symbolic(plan: int, c_row_ptr: int, stream: int) -> int:

@@ -123,6 +123,15 @@ class Plan:
         p._base = self  # keeps the base plan alive
         return p
 
+    def adopt(self, row_ptr: torch.Tensor, nnz: int):
+        """Size this plan from row offsets computed elsewhere
+        (``spgemm_plan_adopt_row_ptr``): ``row_ptr`` (device int32, nrows + 1)
+        holds where each row's entries go in the C arrays later given to
+        ``numeric``; ``nnz`` entries in all.  Blocks on the plan's stream."""
+        nat.spgemm_plan_adopt_row_ptr(self.handle, int(nnz), self.stream)
+        self.row_ptr = row_ptr
+        self.nnz = int(nnz)
+
     def symbolic(self):
         self.row_ptr = torch.empty(self.nrows + 1, dtype=torch.int32, device=self.workspace.device)
         self.nnz = nat.spgemm_symbolic(self.handle, self.row_ptr.data_ptr(), self.stream)
@@ -189,45 +198,26 @@ def spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int 
                    order: str = "rows", **opt_kw):
     """C = A*B with C delivered in pinned host memory.
 
-    Rows of C are independent (Sec. 2.2), so C is computed in ``chunks`` row
-    ranges of about equal shares of A's nonzeros, each a plan sharing one
-    preprocessing of B (``spgemm_analyse_rows``).  After all ranges are sized,
-    the ranges' numeric passes run on ``streams`` compute streams while a
-    copy stream brings finished ranges to the host, so the device-to-host
-    copy of C overlaps the computation; only the first range's computation
-    and the last range's copy are not hidden.  Each range waits for its own
-    longest rows, which one whole-matrix pass would overlap with other work,
-    so a few ranges (default 4, one compute stream) do best on power-law
-    matrices.  ``order="products"`` computes the lightest range first, the
-    second lightest last and the others heaviest first (``"rows"``: row
-    order).  ``out`` = (row_ptr, col_idx, vals) pinned CPU tensors
-    to fill, reused when large enough.  Returns CPU tensors (row_ptr,
-    col_idx, vals); blocks until they are complete."""
+    One plan over all rows analyses the product and sizes C (one symbolic
+    pass).  Rows of C are independent (Sec. 2.2), so the numeric pass then
+    runs in ``chunks`` row ranges of about equal output, each a plan sharing
+    the whole plan's preprocessing of B (``spgemm_analyse_rows``) and sized
+    from the whole row pointer (``spgemm_plan_adopt_row_ptr``), so it writes
+    its rows in place; a copy stream brings each finished range to the host
+    while later ranges compute on ``streams`` compute streams.  Only the first
+    range's computation and the last range's copy are not hidden.
+    ``order="products"`` computes the lightest range first, the second
+    lightest last and the others heaviest first (``"rows"``: row order).
+    ``out`` = (row_ptr, col_idx, vals) pinned CPU tensors to fill, reused when
+    large enough.  Returns CPU tensors (row_ptr, col_idx, vals); blocks until
+    they are complete."""
     dev = A.row_ptr.device
     comp = torch.cuda.current_stream(dev)
     copy = _stream_pool(dev, "copy", 1)[0]
     work = _stream_pool(dev, "compute", max(1, int(streams)))
     m = A.nrows
-    base = Plan(A, B, dtype=dtype, row_range=(0, 0), **opt_kw)  # B's run lists only
-    k = max(1, min(int(chunks), m))
-    targets = (torch.arange(1, k, device=dev, dtype=torch.int64) * A.nnz // k).to(torch.int32)
-    cuts = torch.searchsorted(A.row_ptr, targets).cpu().tolist() if k > 1 else []
-    bounds = sorted(set([0, m] + [min(max(int(c), 0), m) for c in cuts]))
-    ranges = [(rb, re) for rb, re in zip(bounds[:-1], bounds[1:]) if re > rb]
-    a_vals = A.vals.to(dtype)
-    b_vals = B.vals.to(dtype)
-    ready = torch.cuda.Event()
-    ready.record(comp)  # inputs, their values in dtype and B's run lists
-    for s in work:
-        s.wait_event(ready)
-    plans, nnzs = [], []
-    for i, (rb, re) in enumerate(ranges):
-        with torch.cuda.stream(work[i % len(work)]):  # the plan's workspace and C's row pointer live there
-            pl = base.rows(rb, re)
-            plans.append(pl)
-            nnzs.append(pl.symbolic()[1])
-    offs = np.concatenate([[0], np.cumsum(nnzs)]).astype(np.int64)
-    total = int(offs[-1])
+    base = Plan(A, B, dtype=dtype, **opt_kw)
+    rp, total = base.symbolic()
     if total >= 2**31:
         raise nat.SpgemmError("nnz(C) does not fit int32")
     if out is None or out[0].numel() < m + 1 or out[1].numel() < total or out[2].numel() < total:
@@ -235,6 +225,34 @@ def spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int 
                torch.empty(max(total, 1), dtype=torch.int32).pin_memory(),
                torch.empty(max(total, 1), dtype=dtype).pin_memory())
     h_rp, h_ci, h_v = out
+    # ranges of about equal output
+    k = max(1, min(int(chunks), m))
+    if k > 1:
+        targets = (torch.arange(1, k, device=dev, dtype=torch.int64) * total // k).to(torch.int32)
+        cuts = torch.searchsorted(rp, targets).cpu().tolist()
+    else:
+        cuts = []
+    bounds = sorted(set([0, m] + [min(max(int(c), 0), m) for c in cuts]))
+    offs = rp[torch.tensor(bounds, device=dev)].cpu().tolist()
+    ranges = [(bounds[i], bounds[i + 1], offs[i], offs[i + 1] - offs[i]) for i in range(len(bounds) - 1)
+              if bounds[i + 1] > bounds[i]]
+    ci = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+    v = torch.empty(max(total, 1), dtype=dtype, device=dev)
+    a_vals = A.vals.to(dtype)
+    b_vals = B.vals.to(dtype)
+    ready = torch.cuda.Event()
+    ready.record(comp)  # inputs, their values in dtype, B's run lists, C's row pointer
+    copy.wait_event(ready)
+    with torch.cuda.stream(copy):
+        h_rp[:m + 1].copy_(rp, non_blocking=True)
+    for s in work:
+        s.wait_event(ready)
+    plans = []
+    for i, (rb, re, o, n) in enumerate(ranges):
+        with torch.cuda.stream(work[i % len(work)]):  # the plan's workspace lives there
+            pl = base.rows(rb, re)
+            pl.adopt(rp[rb:re + 1], n)
+            plans.append(pl)
     if order == "products" and len(plans) > 2:
         # the range computed first and the range copied last are not hidden:
         # make them the two lightest, heavy ranges in between
@@ -244,27 +262,20 @@ def spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int 
     else:
         seq = list(range(len(plans)))
     for idx in seq:
-        pl, (rb, re) = plans[idx], ranges[idx]
-        o, n = int(offs[idx]), nnzs[idx]
+        pl, (rb, re, o, n) = plans[idx], ranges[idx]
         ws = work[idx % len(work)]
         with torch.cuda.stream(ws):
-            ci, v = pl.numeric(a_vals, b_vals)
+            pl.numeric(a_vals, b_vals, col_idx=ci, vals=v)
         done = torch.cuda.Event()
         done.record(ws)
         copy.wait_event(done)
-        with torch.cuda.stream(copy):
-            h_rp[rb:re].copy_(pl.row_ptr[:re - rb], non_blocking=True)
-            if n:
-                h_ci[o:o + n].copy_(ci, non_blocking=True)
-                h_v[o:o + n].copy_(v, non_blocking=True)
-        for t in (ci, v, pl.row_ptr):
-            t.record_stream(copy)
+        if n:
+            with torch.cuda.stream(copy):
+                h_ci[o:o + n].copy_(ci[o:o + n], non_blocking=True)
+                h_v[o:o + n].copy_(v[o:o + n], non_blocking=True)
+    for t in (ci, v, rp):
+        t.record_stream(copy)
     copy.synchronize()
-    rp = h_rp.numpy()
-    for idx, (rb, re) in enumerate(ranges):
-        if offs[idx]:
-            rp[rb:re] += np.int32(offs[idx])
-    rp[m] = total
     for pl in plans:
         pl.close()
     base.close()

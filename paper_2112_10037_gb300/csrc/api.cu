@@ -467,6 +467,21 @@ spgemm_status spgemm_symbolic(spgemm_plan* p, int32_t* c_row_ptr, int64_t* c_nnz
   return SPGEMM_OK;
 }
 
+spgemm_status spgemm_plan_adopt_row_ptr(spgemm_plan* p, int64_t nnz, spgemm_stream_t stream) {
+  if (!p || nnz < 0) return SPGEMM_ERR_INVALID_ARG;
+  if (nnz >= (1ll << 31)) return SPGEMM_ERR_INDEX_OVERFLOW;
+  // split rows take their per-window offsets from the symbolic pass
+  if (p->sp.heavy_bin < sg::NBINS && p->sp.hcap > 0) return SPGEMM_ERR_NOT_READY;
+  cudaStream_t st = (cudaStream_t)stream;
+  spgemm_status s = read_stats(p, st);  // rows per path, and any error of the analysis
+  if (s != SPGEMM_OK) return s;
+  s = from_err_word(p->host_st.err);
+  if (s != SPGEMM_OK) return s;
+  p->nnz_c = nnz;
+  p->symbolic_done = true;
+  return SPGEMM_OK;
+}
+
 spgemm_status spgemm_numeric(spgemm_plan* p, const void* a_vals, const void* b_vals, const int32_t* c_row_ptr,
                              int32_t* c_col_idx, void* c_vals, spgemm_stream_t stream) {
   if (!p) return SPGEMM_ERR_INVALID_ARG;

@@ -84,3 +84,18 @@ def test_row_plans_share_b(api, oracle_mod):
         assert_values_close(C.vals, sub.vals, ssub.vals)
         pl.close()
     base.close()
+
+
+def test_adopt_refuses_split_rows(api):
+    """Split rows take their per-window offsets from the symbolic pass, so a
+    plan with split rows cannot be sized from a row pointer alone."""
+    from paper_2112_10037_gb300 import _native as nat
+    A = gen.rmat(11, 8)
+    dA = api.DeviceCSR.from_host(A)
+    base = api.Plan(dA, dA, split_min=128, num_block_min=-1)
+    rp, nnz = base.symbolic()
+    pl = base.rows(0, A.nrows)
+    with pytest.raises(nat.SpgemmError):
+        pl.adopt(rp, nnz)
+    pl.close()
+    base.close()
