@@ -41,11 +41,22 @@ static cudaError_t warp_num(const LaunchCtx& c, const Csr& A, const Csr& B, cons
   ns.runs = sp.runs;
   ns.hcnt = sp.hcnt;
   ns.counter = &c.st->work[0];
+  // rows of at most 32 nonzeros first (one cursor per lane, next window's
+  // loads overlapped with this window's emission), then the others
+  auto k1 = k_num_warp1<W, NUM_WARPS_CTA, T>;
+  const int occ1 = kernel_blocks_per_sm(k1, NUM_WARPS_CTA * 32, smem);
+  if (occ1 <= 0) return cudaErrorInvalidConfiguration;
+  unsigned* counter1 = &c.st->work[3];
   cudaError_t e = cudaMemsetAsync(ns.counter, 0, sizeof(unsigned), c.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(counter1, 0, sizeof(unsigned), c.stream);
   if (e != cudaSuccess) return e;
+  k1<<<c.nsm * occ1, NUM_WARPS_CTA * 32, smem, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, ns, c_rp, c_ci, c_v,
+                                                           counter1, c.err);
+  count_launch(c);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int grid = c.nsm * occ;
   k<<<grid, NUM_WARPS_CTA * 32, smem, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, ns, cur, nxt, c_rp, c_ci, c_v,
-                                                  c.err);
+                                                  c.err, 1);
   count_launch(c);
   return cudaGetLastError();
 }

@@ -78,13 +78,11 @@ struct WarpWin {
     }
   }
 
-  // Products of segments [s, s+len) of B with multiplier a (one segment per
-  // lane), columns relative to base.  Long segments are walked by the whole
-  // warp; short ones are flattened so each lane takes one product.
-  __device__ __forceinline__ void segments(const Csr& B, const T* __restrict__ bv, int s, int len, T a,
-                                           int base) {
+  // Products of long segments (at least 32 entries; one segment per lane,
+  // the others skipped): the whole warp walks one segment at a time.
+  __device__ __forceinline__ void long_segments(const Csr& B, const T* __restrict__ bv, int s, int len, T a,
+                                                int base) {
     const int lane = lane_id();
-    if (!__any_sync(FULL, len > 0)) return;
     unsigned lm = __ballot_sync(FULL, len >= 32);
     while (lm) {
       const int L = __ffs(lm) - 1;
@@ -103,33 +101,86 @@ struct WarpWin {
       for (; t < ln; t += 32) add_distinct(B.ci[ls + t] - base, la, bv[ls + t], true);
       __syncwarp();
     }
+  }
+
+  // Short segments (fewer than 32 entries) are flattened so every lane takes
+  // one product.  flat_gather places the first 64 products and issues their
+  // loads; flat_apply adds them (and any further products).  Splitting the
+  // two lets a caller issue a later window's loads before it emits this one.
+  struct Flat {
+    int tot, incl, excl, j0, j1;
+    T b0, b1, a0, a1;
+  };
+
+  __device__ __forceinline__ void flat_gather(const Csr& B, const T* __restrict__ bv, int s, int len, T a, int base,
+                                              Flat& f) {
+    const int lane = lane_id();
     const int sl = len < 32 ? len : 0;
-    const int incl = warp_incl_scan(sl);
-    const int tot = __shfl_sync(FULL, incl, 31);
-    const int excl = incl - sl;
-    for (int p0 = 0; p0 < tot; p0 += 64) {
+    f.incl = warp_incl_scan(sl);
+    f.tot = __shfl_sync(FULL, f.incl, 31);
+    f.excl = f.incl - sl;
+    f.j0 = f.j1 = 0;
+    f.b0 = f.b1 = f.a0 = f.a1 = T(0);
+    if (f.tot == 0) return;
+    const int p = lane, p2 = lane + 32;
+    const int o = warp_owner(f.incl, p), o2 = warp_owner(f.incl, p2);
+    const int os = __shfl_sync(FULL, s, o), oex = __shfl_sync(FULL, f.excl, o);
+    f.a0 = __shfl_sync(FULL, a, o);
+    const int os2 = __shfl_sync(FULL, s, o2), oex2 = __shfl_sync(FULL, f.excl, o2);
+    f.a1 = __shfl_sync(FULL, a, o2);
+    if (p < f.tot) {
+      const int bi = os + p - oex;
+      f.j0 = B.ci[bi] - base;
+      f.b0 = bv[bi];
+    }
+    if (p2 < f.tot) {
+      const int bi = os2 + p2 - oex2;
+      f.j1 = B.ci[bi] - base;
+      f.b1 = bv[bi];
+    }
+  }
+
+  // s, a: the same lane values flat_gather had.
+  __device__ __forceinline__ void flat_apply(const Csr& B, const T* __restrict__ bv, int s, T a, int base,
+                                             const Flat& f) {
+    const int lane = lane_id();
+    if (f.tot == 0) return;
+    add_atomic(f.j0, f.a0, f.b0, lane < f.tot);
+    add_atomic(f.j1, f.a1, f.b1, lane + 32 < f.tot);
+    for (int p0 = 64; p0 < f.tot; p0 += 64) {
       const int p = p0 + lane, p2 = p + 32;
-      const int o = warp_owner(incl, p), o2 = warp_owner(incl, p2);
-      const int os = __shfl_sync(FULL, s, o), oex = __shfl_sync(FULL, excl, o);
+      const int o = warp_owner(f.incl, p), o2 = warp_owner(f.incl, p2);
+      const int os = __shfl_sync(FULL, s, o), oex = __shfl_sync(FULL, f.excl, o);
       const T oa = __shfl_sync(FULL, a, o);
-      const int os2 = __shfl_sync(FULL, s, o2), oex2 = __shfl_sync(FULL, excl, o2);
+      const int os2 = __shfl_sync(FULL, s, o2), oex2 = __shfl_sync(FULL, f.excl, o2);
       const T oa2 = __shfl_sync(FULL, a, o2);
       int j = 0, j2 = 0;
       T b = T(0), b2 = T(0);
-      if (p < tot) {
+      if (p < f.tot) {
         const int bi = os + p - oex;
         j = B.ci[bi] - base;
         b = bv[bi];
       }
-      if (p2 < tot) {
+      if (p2 < f.tot) {
         const int bi = os2 + p2 - oex2;
         j2 = B.ci[bi] - base;
         b2 = bv[bi];
       }
-      add_atomic(j, oa, b, p < tot);
-      add_atomic(j2, oa2, b2, p2 < tot);
+      add_atomic(j, oa, b, p < f.tot);
+      add_atomic(j2, oa2, b2, p2 < f.tot);
     }
     __syncwarp();
+  }
+
+  // Products of segments [s, s+len) of B with multiplier a (one segment per
+  // lane), columns relative to base.
+  __device__ __forceinline__ void segments(const Csr& B, const T* __restrict__ bv, int s, int len, T a,
+                                           int base) {
+    if (!__any_sync(FULL, len > 0)) return;
+    long_segments(B, bv, s, len, a, base);
+    Flat f;
+    flat_gather(B, bv, s, len, a, base, f);
+    flat_apply(B, bv, s, a, base, f);
   }
 
   // Emits the window [base, base + ncols) in column order at c_ci/c_v + out
@@ -191,7 +242,8 @@ template <int W, int NWARP, typename T>
 __global__ void __launch_bounds__(NWARP * 32)
 k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri, const DevStats* st,
            int bin_lo, int bin_hi, NumSplit sp, int32_t* __restrict__ gcur, int32_t* __restrict__ gnxt,
-           const int32_t* __restrict__ c_rp, int32_t* __restrict__ c_ci, T* __restrict__ c_v, uint32_t* err) {
+           const int32_t* __restrict__ c_rp, int32_t* __restrict__ c_ci, T* __restrict__ c_v, uint32_t* err,
+           int skip_small) {
   static_assert(W % 512 == 0, "window must be a multiple of 512 columns");
   constexpr size_t WB = (size_t)W * sizeof(T) + W / 8;  // per-warp bytes
   constexpr int WSHIFT = (W == 512) ? 9 : (W == 1024) ? 10 : (W == 2048) ? 11 : (W == 4096) ? 12 : 13;
@@ -278,6 +330,7 @@ k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
     const int r = ri.rows[idx];
     const long long i = ri.row_begin + r;
     const int a0 = A.rp[i], a1 = A.rp[i + 1], nA = a1 - a0;
+    if (skip_small && nA <= 32) continue;  // k_num_warp1 takes the row
     const int cmx = ri.cmax[r];
     const long long rbeg = c_rp[r];
     const int out_end = (int)(c_rp[r + 1] - rbeg);
@@ -377,6 +430,103 @@ k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
         out += win.emit(base, ncols, out, out_end, rci, rcv);
         w = warp_min(mn);
       }
+    }
+    if (lane == 0 && out != out_end) atomicOr(err, EB_INTERNAL);
+  }
+}
+
+// Rows of at most 32 nonzeros of A (not split): one cursor per lane, and the
+// next window's short-segment products are placed and their loads issued
+// before this window is emitted, so the emission hides their latency.  Same
+// accumulator, emission and result as k_num_warp.
+template <int W, int NWARP, typename T>
+__global__ void __launch_bounds__(NWARP * 32)
+k_num_warp1(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri, const DevStats* st,
+            int bin_lo, int bin_hi, NumSplit sp, const int32_t* __restrict__ c_rp, int32_t* __restrict__ c_ci,
+            T* __restrict__ c_v, unsigned* counter, uint32_t* err) {
+  constexpr size_t WB = (size_t)W * sizeof(T) + W / 8;  // per-warp bytes
+  constexpr int WSHIFT = (W == 512) ? 9 : (W == 1024) ? 10 : (W == 2048) ? 11 : (W == 4096) ? 12 : 13;
+  static_assert((1 << WSHIFT) == W, "window must be a power of two");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_lb, s_le, s_nh;
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  WarpWin<W, T> win;
+  win.acc = reinterpret_cast<T*>(smem_raw + (size_t)warp * WB);
+  win.bits = reinterpret_cast<uint32_t*>(smem_raw + (size_t)warp * WB + (size_t)W * sizeof(T));
+  win.err = err;
+  for (int t = lane; t < W; t += 32) win.acc[t] = T(0);
+  for (int t = lane; t < W / 32; t += 32) win.bits[t] = 0u;
+  if (threadIdx.x == 0) {
+    int b, e;
+    bin_range(st, bin_lo, bin_hi, &b, &e);
+    s_lb = b;
+    s_le = e;
+    // split rows are the leading rows of the range (k_num_warp takes them)
+    int nh = 0, hb = 0, he = 0;
+    if (sp.heavy_bin < NBINS && sp.hi_bin >= sp.heavy_bin && sp.heavy_bin >= bin_lo && sp.hi_bin == bin_hi) {
+      bin_range(st, sp.heavy_bin, sp.hi_bin, &hb, &he);
+      if (hb == b) nh = he - hb;
+    }
+    s_nh = nh < sp.hcap ? nh : sp.hcap;
+  }
+  if (block_skip(st)) return;
+  const int lb = s_lb, le = s_le, nh = s_nh;
+  while (true) {
+    long long item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1u);
+    item = __shfl_sync(FULL, item, 0);
+    const long long idx = (long long)lb + nh + item;
+    if (idx >= le) break;
+    const int r = ri.rows[idx];
+    const long long i = ri.row_begin + r;
+    const int a0 = A.rp[i], a1 = A.rp[i + 1];
+    if (a1 - a0 > 32) continue;  // k_num_warp takes the row
+    const int cmx = ri.cmax[r];
+    const long long rbeg = c_rp[r];
+    const int out_end = (int)(c_rp[r + 1] - rbeg);
+    int32_t* const rci = c_ci + rbeg;
+    T* const rcv = c_v + rbeg;
+    // this lane's nonzero: its current run (window wid, segment [s0, s1))
+    int rj = 0, wid = INT_MAX, s0 = 0, s1 = 0;
+    T a = T(0);
+    const int e = a0 + lane;
+    if (e < a1) {
+      const int k = A.ci[e];
+      a = av[e];
+      rj = sp.rr[k];
+      const int2 c0 = sp.runs[rj];
+      wid = c0.x;
+      s0 = c0.y;
+      if (c0.x != INT_MAX) s1 = sp.runs[rj + 1].y;  // empty rows hold only the sentinel
+    }
+    int w = warp_min(wid);
+    typename WarpWin<W, T>::Flat f;
+    if (w != INT_MAX) win.flat_gather(B, bv, s0, wid == w ? s1 - s0 : 0, a, w << WSHIFT, f);
+    int out = 0;
+    while (w != INT_MAX) {
+      const int base = w << WSHIFT;
+      const bool act = wid == w;
+      // loads of this lane's next run, for the advance below
+      int2 nx = make_int2(wid, s0);
+      int nend = s1;
+      if (act) {
+        nx = sp.runs[rj + 1];
+        if (nx.x != INT_MAX) nend = sp.runs[rj + 2].y;
+      }
+      const int len = act ? s1 - s0 : 0;
+      win.long_segments(B, bv, s0, len, a, base);
+      win.flat_apply(B, bv, s0, a, base, f);
+      if (act) {
+        ++rj;
+        wid = nx.x;
+        s0 = nx.y;
+        s1 = nend;
+      }
+      const int wn = warp_min(wid);
+      if (wn != INT_MAX) win.flat_gather(B, bv, s0, wid == wn ? s1 - s0 : 0, a, wn << WSHIFT, f);
+      const int ncols = min(W, cmx - base + 1);
+      out += win.emit(base, ncols, out, out_end, rci, rcv);
+      w = wn;
     }
     if (lane == 0 && out != out_end) atomicOr(err, EB_INTERNAL);
   }
