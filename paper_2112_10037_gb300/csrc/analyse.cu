@@ -52,14 +52,35 @@ __global__ void __launch_bounds__(256) k_analyse(Csr A, Csr B, long long row_beg
     const int a0 = A.rp[i], a1 = A.rp[i + 1];
     long long p = 0;
     int mn = INT_MAX, mx = -1;
-    for (int e = a0 + lane; e < a1; e += 32) {
-      const int k = A.ci[e];
-      if (k < 0 || (long long)k >= B.nrows) { bad = true; continue; }
-      const int s = B.rp[k], t = B.rp[k + 1];
-      if (t > s) {
-        p += t - s;
-        mn = min(mn, B.ci[s]);
-        mx = max(mx, B.ci[t - 1]);
+    // four entries per lane per step, their dependent loads in flight
+    // together (long rows of power-law matrices otherwise form the tail)
+    for (int e0 = a0 + lane; e0 < a1; e0 += 128) {
+      int kk[4], ss[4], tt[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + 32 * u;
+        kk[u] = e < a1 ? A.ci[e] : -1;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = e0 + 32 * u;
+        ss[u] = tt[u] = 0;
+        if (e < a1) {
+          if (kk[u] < 0 || (long long)kk[u] >= B.nrows) {
+            bad = true;
+          } else {
+            ss[u] = B.rp[kk[u]];
+            tt[u] = B.rp[kk[u] + 1];
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (tt[u] > ss[u]) {
+          p += tt[u] - ss[u];
+          mn = min(mn, B.ci[ss[u]]);
+          mx = max(mx, B.ci[tt[u] - 1]);
+        }
       }
     }
     p = warp_sum(p);
@@ -141,16 +162,23 @@ __global__ void __launch_bounds__(256) k_runs_count(Csr B, int s1, int32_t* __re
   for (long long k = w; k < B.nrows; k += nw) {
     const int rs = B.rp[k], re = B.rp[k + 1];
     int n1 = 0, n2 = 0;
-    for (int base = rs; base < re; base += 32) {
-      const int idx = base + lane;
-      bool b1 = false, b2 = false;
-      if (idx < re) {
-        const int c = B.ci[idx], pc = idx == rs ? -1 : B.ci[idx - 1];
-        b1 = idx == rs || (pc >> s1) != (c >> s1);
-        b2 = idx == rs || (pc >> s2) != (c >> s2);
+    for (int base = rs; base < re; base += 128) {  // 4 chunks of loads in flight per step
+      int c[4], pc[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + 32 * u + lane;
+        c[u] = idx < re ? B.ci[idx] : 0;
+        pc[u] = (idx < re && idx > rs) ? B.ci[idx - 1] : -1;
       }
-      n1 += __popc(__ballot_sync(FULL, b1));
-      n2 += __popc(__ballot_sync(FULL, b2));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int idx = base + 32 * u + lane;
+        const bool in = idx < re;
+        const bool b1 = in && (idx == rs || (pc[u] >> s1) != (c[u] >> s1));
+        const bool b2 = in && (idx == rs || (pc[u] >> s2) != (c[u] >> s2));
+        n1 += __popc(__ballot_sync(FULL, b1));
+        n2 += __popc(__ballot_sync(FULL, b2));
+      }
     }
     if (lane == 0) {
       rr1[k] = n1 + 1;
@@ -164,17 +192,23 @@ __device__ __forceinline__ void runs_fill_row(const Csr& B, int k, int shift, co
   const int lane = lane_id();
   const int rs = B.rp[k], re = B.rp[k + 1];
   int pos = rr[k];
-  for (int base = rs; base < re; base += 32) {
-    const int idx = base + lane;
-    bool start = false;
-    int wid = 0;
-    if (idx < re) {
-      wid = B.ci[idx] >> shift;
-      start = idx == rs || (B.ci[idx - 1] >> shift) != wid;
+  for (int base = rs; base < re; base += 128) {  // 4 chunks of loads in flight per step
+    int c[4], pc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + 32 * u + lane;
+      c[u] = idx < re ? B.ci[idx] : 0;
+      pc[u] = (idx < re && idx > rs) ? B.ci[idx - 1] : -1;
     }
-    const unsigned m = __ballot_sync(FULL, start);
-    if (start) runs[pos + __popc(m & lanemask_lt())] = make_int2(wid, idx);
-    pos += __popc(m);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + 32 * u + lane;
+      const int wid = c[u] >> shift;
+      const bool start = idx < re && (idx == rs || (pc[u] >> shift) != wid);
+      const unsigned m = __ballot_sync(FULL, start);
+      if (start) runs[pos + __popc(m & lanemask_lt())] = make_int2(wid, idx);
+      pos += __popc(m);
+    }
   }
   if (lane == 0) runs[rr[k + 1] - 1] = make_int2(INT_MAX, re);
 }
