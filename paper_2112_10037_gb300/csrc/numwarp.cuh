@@ -185,38 +185,57 @@ struct WarpWin {
 
   // Emits the window [base, base + ncols) in column order at c_ci/c_v + out
   // (offsets relative to the row's first entry, checked against out_end),
-  // clears it, returns the number of entries.  Lanes take 32-column words;
-  // a warp prefix of their popcounts places each lane's entries.
-  __device__ __forceinline__ int emit(int base, int ncols, int out, int out_end, int32_t* __restrict__ c_ci,
-                                      T* __restrict__ c_v) {
+  // clears it, returns the number of entries.  Lanes take consecutive outputs
+  // (the word of an output from a warp search over the words' popcount
+  // prefix, its bit from a binary search on popcounts inside the word), so a
+  // window takes ceil(entries / 32) steps and the stores of C are coalesced.
+  __device__ __forceinline__ int emit(int base, int ncols, int out, int out_end,
+                                                int32_t* __restrict__ c_ci, T* __restrict__ c_v) {
     const int lane = lane_id();
-    const int start = out;
     const int nw = (ncols + 31) >> 5;
     __syncwarp();
+    int total = 0;
     for (int wb = 0; wb < nw; wb += 32) {
       const int wi = wb + lane;
-      uint32_t m = wi < nw ? bits[wi] : 0u;
-      const int cnt = __popc(m);
-      const int inc = warp_incl_scan(cnt);
-      int pos = out + inc - cnt;
-      if (m) bits[wi] = 0u;
-      while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        const int jj = (wi << 5) + b;
-        if (pos < out_end) {  // C is written once: streaming stores keep B resident in L2
-          __stcs(c_ci + pos, base + jj);
-          __stcs(c_v + pos, acc[jj]);
-        } else {
-          atomicOr(err, EB_INTERNAL);
+      const uint32_t m = wi < nw ? bits[wi] : 0u;
+      const int c = __popc(m);
+      const int inc = warp_incl_scan(c);
+      const int tot = __shfl_sync(FULL, inc, 31);
+      const int exc = inc - c;
+      for (int t0 = 0; t0 < tot; t0 += 32) {
+        const int t = t0 + lane;
+        const int o = warp_owner(inc, t);
+        const uint32_t mo = __shfl_sync(FULL, m, o & 31);
+        const int eo = __shfl_sync(FULL, exc, o & 31);
+        if (t < tot) {
+          uint32_t x = mo;
+          int rank = t - eo, bit = 0;
+#pragma unroll
+          for (int sh = 16; sh >= 1; sh >>= 1) {
+            const int lowc = __popc(x & ((1u << sh) - 1u));
+            if (rank >= lowc) {
+              rank -= lowc;
+              x >>= sh;
+              bit += sh;
+            }
+          }
+          const int jj = ((wb + o) << 5) + bit;
+          const T v = acc[jj];
+          acc[jj] = T(0);
+          const int pos = out + total + t;
+          if (pos < out_end) {
+            __stcs(c_ci + pos, base + jj);
+            __stcs(c_v + pos, v);
+          } else {
+            atomicOr(err, EB_INTERNAL);
+          }
         }
-        acc[jj] = T(0);
-        ++pos;
       }
-      out += __shfl_sync(FULL, inc, 31);
+      if (m) bits[wi] = 0u;  // each lane clears the word it read; others used a shuffled copy
+      total += tot;
     }
     __syncwarp();
-    return out - start;
+    return total;
   }
 };
 
