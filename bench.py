@@ -396,7 +396,8 @@ def run_e2e(args, api, torch, dev, A, B, kw, products):
     h2d = A.row_ptr.nbytes + A.col_idx.nbytes + A.vals.nbytes
     d2h = 4 * nrp + 12 * nnz
     return {"value": round(2.0 * products / (ms / 1e3) / 1e9, 2), "unit": "GFLOP/s",
-            "ms_per_step": round(ms, 3), "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+            "ms_per_step": round(ms, 3), "ms_steps": [round(t, 3) for t in ts],
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
 
 # ------------------------------------------------------- reference arm

@@ -149,17 +149,11 @@ __device__ __forceinline__ V warp_sum(V v) {
   return v;
 }
 
-__device__ __forceinline__ int warp_min(int v) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v = min(v, __shfl_xor_sync(FULL, v, d));
-  return v;
-}
-
-__device__ __forceinline__ int warp_max(int v) {
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) v = max(v, __shfl_xor_sync(FULL, v, d));
-  return v;
-}
+// 32-bit integer reductions are single warp instructions (redux.sync).
+__device__ __forceinline__ int warp_sum(int v) { return __reduce_add_sync(FULL, v); }
+__device__ __forceinline__ unsigned warp_sum(unsigned v) { return __reduce_add_sync(FULL, v); }
+__device__ __forceinline__ int warp_min(int v) { return __reduce_min_sync(FULL, v); }
+__device__ __forceinline__ int warp_max(int v) { return __reduce_max_sync(FULL, v); }
 
 // acc += v on a shared-memory word, result unused (a reduction, not a fetch).
 __device__ __forceinline__ void red_add_shared(double* p, double v) {
