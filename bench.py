@@ -369,7 +369,7 @@ def run_e2e(args, api, torch, dev, A, B, kw, products):
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_rp, h_ci, h_v = pin(A.row_ptr), pin(A.col_idx), pin(A.vals)
     stream = torch.cuda.current_stream()
-    steps = max(1, min(args.steps, 3))
+    steps = max(3, min(args.steps, 5))
 
     def once(out=None):
         d_rp = h_rp.to(dev, non_blocking=True)
@@ -381,7 +381,10 @@ def run_e2e(args, api, torch, dev, A, B, kw, products):
                                        streams=args.e2e_streams, out=out, order=args.e2e_order, **kw)
         return (rp, ci, v), ci.numel(), rp.numel()
 
+    # two untimed calls: the first pins the host buffers and allocates, the
+    # second still pays first-use costs of the copies into fresh buffers
     out, nnz, nrp = once()
+    once(out)
     torch.cuda.synchronize()
     ts = []
     for _ in range(steps):
