@@ -9,6 +9,13 @@
 namespace sg {
 
 constexpr int NUM_WARPS_CTA = 4;  // warps per block on the window path
+// k_num_warp1's warps per block: 9 warps of 1024-column FP64 windows
+// (74.9 KB) let 3 blocks, 27 warps, share an SM's 228 KB of shared memory
+// (4-warp blocks fit 24); wider windows take fewer warps per block.
+template <int W>
+constexpr int num_warps_cta1() {
+  return W <= 1024 ? 9 : (W <= 2048 ? 4 : 2);
+}
 
 static long long rows_in(const int* path_rows, int p) { return path_rows ? path_rows[p] : -1; }
 
@@ -43,14 +50,16 @@ static cudaError_t warp_num(const LaunchCtx& c, const Csr& A, const Csr& B, cons
   ns.counter = &c.st->work[0];
   // rows of at most 32 nonzeros first (one cursor per lane, next window's
   // loads overlapped with this window's emission), then the others
-  auto k1 = k_num_warp1<W, NUM_WARPS_CTA, T>;
-  const int occ1 = kernel_blocks_per_sm(k1, NUM_WARPS_CTA * 32, smem);
+  constexpr int NW1 = num_warps_cta1<W>();
+  auto k1 = k_num_warp1<W, NW1, T>;
+  const size_t smem1 = (size_t)NW1 * ((size_t)W * sizeof(T) + W / 8);
+  const int occ1 = kernel_blocks_per_sm(k1, NW1 * 32, smem1);
   if (occ1 <= 0) return cudaErrorInvalidConfiguration;
   unsigned* counter1 = &c.st->work[3];
   cudaError_t e = cudaMemsetAsync(ns.counter, 0, sizeof(unsigned), c.stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(counter1, 0, sizeof(unsigned), c.stream);
   if (e != cudaSuccess) return e;
-  k1<<<c.nsm * occ1, NUM_WARPS_CTA * 32, smem, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, ns, c_rp, c_ci, c_v,
+  k1<<<c.nsm * occ1, NW1 * 32, smem1, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, ns, c_rp, c_ci, c_v,
                                                            counter1, c.err);
   count_launch(c);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
