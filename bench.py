@@ -272,6 +272,8 @@ def run_ours(args, rank, world, A, B, desc):
     else:
         roof = dict(hbm, bound="hbm", kernel=dom, kernel_ms=round(avg[dom], 4), traffic=traffic)
 
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()  # the device leg's cached blocks; the end-to-end leg allocates its own
     e2e = run_e2e(args, api, torch, dev, A, B, kw, all_products if world == 1 else my_products)
     out = {
         "metric": "SpGEMM GFLOP/s (2*products/s)", "value": round(gflops, 2), "unit": "GFLOP/s",

@@ -6,6 +6,7 @@ library through ``_native``.
 from __future__ import annotations
 
 import dataclasses
+import threading
 from typing import Optional
 
 import numpy as np
@@ -184,6 +185,14 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, dtype=None, **opt_kw) -> DeviceCSR:
 
 
 _streams = {}
+_staging = {}
+_staging_lock = threading.Lock()
+
+
+def release_staging():
+    """Free the device staging buffers that spgemm_to_host keeps between calls."""
+    with _staging_lock:
+        _staging.clear()
 
 
 def _stream_pool(dev, name, n):
@@ -196,6 +205,14 @@ def _stream_pool(dev, name, n):
 
 def spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int = 4, streams: int = 1, out=None,
                    order: str = "rows", **opt_kw):
+    """See _spgemm_to_host; calls on one process are serialised, since they
+    share the device staging buffers (``release_staging`` frees them)."""
+    with _staging_lock:
+        return _spgemm_to_host(A, B, dtype, chunks, streams, out, order, **opt_kw)
+
+
+def _spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int = 4, streams: int = 1, out=None,
+                    order: str = "rows", **opt_kw):
     """C = A*B with C delivered in pinned host memory.
 
     One plan over all rows analyses the product and sizes C (one symbolic
@@ -236,8 +253,15 @@ def spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int 
     offs = rp[torch.tensor(bounds, device=dev)].cpu().tolist()
     ranges = [(bounds[i], bounds[i + 1], offs[i], offs[i + 1] - offs[i]) for i in range(len(bounds) - 1)
               if bounds[i + 1] > bounds[i]]
-    ci = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
-    v = torch.empty(max(total, 1), dtype=dtype, device=dev)
+    # device staging for C, kept between calls (repeated products of one
+    # shape reuse it instead of allocating 12 bytes per entry each time)
+    key = (dev.index, dtype)
+    ci, v = _staging.get(key, (None, None))
+    if ci is None or ci.numel() < max(total, 1):
+        _staging.pop(key, None)
+        ci = torch.empty(max(total, 1), dtype=torch.int32, device=dev)
+        v = torch.empty(max(total, 1), dtype=dtype, device=dev)
+        _staging[key] = (ci, v)
     a_vals = A.vals.to(dtype)
     b_vals = B.vals.to(dtype)
     ready = torch.cuda.Event()
@@ -273,9 +297,10 @@ def spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int 
             with torch.cuda.stream(copy):
                 h_ci[o:o + n].copy_(ci[o:o + n], non_blocking=True)
                 h_v[o:o + n].copy_(v[o:o + n], non_blocking=True)
-    for t in (ci, v, rp):
-        t.record_stream(copy)
+    rp.record_stream(copy)
     copy.synchronize()
+    for s in work:  # the staging buffers are reused by the next call
+        s.synchronize()
     for pl in plans:
         pl.close()
     base.close()
