@@ -49,7 +49,7 @@ typedef enum spgemm_status {
   SPGEMM_ERR_UNSORTED_INPUT = 3,  /* a column index out of range, repeated or descending */
   SPGEMM_ERR_INDEX_OVERFLOW = 4,  /* nnz(C) (or an input nnz) does not fit int32 */
   SPGEMM_ERR_WORKSPACE = 5,       /* workspace NULL or smaller than spgemm_workspace_size */
-  SPGEMM_ERR_TABLE_OVERFLOW = 6,  /* a bounded probe or loop gave up (internal limit) */
+  SPGEMM_ERR_TABLE_OVERFLOW = 6,  /* reserved: not returned by this version */
   SPGEMM_ERR_CUDA = 7,            /* a CUDA runtime call failed */
   SPGEMM_ERR_INTERNAL = 8,
   SPGEMM_ERR_NOT_READY = 9        /* calls out of order (numeric before symbolic) */
@@ -80,8 +80,8 @@ typedef struct spgemm_opts {
   int32_t force_path;  /* -1: automatic.  Testing overrides: 1 (2) sends every row
                           above the register-sort limit to the warp (block) path;
                           3 (4) sends every non-empty row to the warp (block) path */
-  int32_t hash_max;    /* rows of at most this many products use the shared-memory
-                          hash accumulator (0: library default; -1: never) */
+  int32_t hash_max;    /* reserved, ignored: there is no hash accumulator (register
+                          sorts and dense column windows cover every row size) */
   int32_t window_warp; /* columns of the numeric dense window (one per warp):
                           1024, 2048 or 4096 (0: default 1024) */
   int32_t window_block;/* columns of the numeric block window, with block_warps one of
@@ -181,7 +181,8 @@ spgemm_status spgemm_numeric(spgemm_plan* plan, const void* a_vals, const void* 
 
 /* Work statistics of an analysed plan (blocks on `stream` to read them):
  * total and largest per-row product count, and the number of rows sent to
- * the register-sort, hash, warp and block paths.  Any output may be NULL. */
+ * the register-sort, hash (always 0: no such path), warp and block paths of
+ * the symbolic pass.  Any output may be NULL. */
 spgemm_status spgemm_plan_stats(spgemm_plan* plan, spgemm_stream_t stream,
                                 int64_t* total_products, int64_t* max_row_products,
                                 int64_t* rows_per_path /* 4 entries */);
@@ -193,7 +194,7 @@ spgemm_status spgemm_plan_stats(spgemm_plan* plan, spgemm_stream_t stream,
  * in ms[0..n-1], in this order: analyse, symbolic register-sort, symbolic
  * hash, symbolic warp, symbolic block, scan, numeric register-sort, numeric
  * hash, numeric warp, numeric block (SPGEMM_TIMER_COUNT entries; groups
- * never run read as 0).  Creating the events is the only resource this
+ * never run, such as the two hash groups, read as 0).  Creating the events is the only resource this
  * allocates (host-side event handles). */
 #define SPGEMM_TIMER_COUNT 10
 spgemm_status spgemm_plan_set_profiling(spgemm_plan* plan, int on);

@@ -156,7 +156,7 @@ class Plan:
 
     def stats(self):
         """(total products, largest row's products, rows per path
-        [register-sort, hash, warp, block])."""
+        [register-sort, hash (always 0), warp, block] of the symbolic pass)."""
         return nat.spgemm_plan_stats(self.handle, self.stream)
 
     def check(self):

@@ -380,7 +380,7 @@ const char* spgemm_status_string(spgemm_status s) {
     case SPGEMM_ERR_UNSORTED_INPUT: return "column indices out of range, repeated or not ascending";
     case SPGEMM_ERR_INDEX_OVERFLOW: return "index overflow (a count does not fit int32)";
     case SPGEMM_ERR_WORKSPACE: return "workspace missing or too small";
-    case SPGEMM_ERR_TABLE_OVERFLOW: return "bounded probe limit reached";
+    case SPGEMM_ERR_TABLE_OVERFLOW: return "reserved status";
     case SPGEMM_ERR_CUDA: return "CUDA runtime error";
     case SPGEMM_ERR_INTERNAL: return "internal error";
     case SPGEMM_ERR_NOT_READY: return "call out of order";
