@@ -39,13 +39,15 @@ __global__ void __launch_bounds__(256) k_analyse(Csr A, Csr B, long long row_beg
                                                  int* __restrict__ cmax, DevStats* st) {
   __shared__ int s_hist[NBINS];
   __shared__ unsigned long long s_total, s_max;
+  __shared__ unsigned s_wide;
   if (threadIdx.x < NBINS) s_hist[threadIdx.x] = 0;
-  if (threadIdx.x == 0) { s_total = 0; s_max = 0; }
+  if (threadIdx.x == 0) { s_total = 0; s_max = 0; s_wide = 0; }
   if (block_skip(st)) return;  // validated input was rejected
   const int lane = lane_id();
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
   unsigned long long my_total = 0, my_max = 0;
+  unsigned my_wide = 0;
   bool bad = false;
   for (long long r = w; r < mloc; r += nw) {
     const long long i = row_begin + r;
@@ -87,6 +89,7 @@ __global__ void __launch_bounds__(256) k_analyse(Csr A, Csr B, long long row_beg
     mn = warp_min(mn);
     mx = warp_max(mx);
     if (lane == 0) {
+      my_wide += a1 - a0 > 32 ? 1u : 0u;
       prod[r] = p;
       cmin[r] = mn;
       cmax[r] = mx;
@@ -99,6 +102,7 @@ __global__ void __launch_bounds__(256) k_analyse(Csr A, Csr B, long long row_beg
     atomicAdd(&s_total, my_total);
     atomicMax(&s_max, my_max);
   }
+  if (lane == 0 && my_wide) atomicAdd(&s_wide, my_wide);
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(&st->err, EB_UNSORTED);
   __syncthreads();
   if (threadIdx.x < NBINS && s_hist[threadIdx.x]) atomicAdd(&st->hist[threadIdx.x], s_hist[threadIdx.x]);
@@ -106,6 +110,7 @@ __global__ void __launch_bounds__(256) k_analyse(Csr A, Csr B, long long row_beg
     atomicAdd(&st->total_products, s_total);
     atomicMax(&st->max_products, s_max);
   }
+  if (threadIdx.x == 0 && s_wide) atomicAdd(&st->rows_wide, s_wide);
 }
 
 // Counting sort of the non-empty rows by bin, largest bin first.  Each block

@@ -492,7 +492,8 @@ spgemm_status spgemm_numeric(spgemm_plan* p, const void* a_vals, const void* b_v
   sg::LaunchCtx c = ctx_of(p, stream);
   const sg::RowInfo ri = rowinfo_of(p);
   cudaError_t e = sg::launch_numeric(c, p->A, p->B, ri, p->pb, p->tu, p->sp, p->opts.dtype, a_vals, b_vals,
-                                     p->cursor, p->nxt, c_row_ptr, c_col_idx, c_vals, p->path_rows);
+                                     p->cursor, p->nxt, c_row_ptr, c_col_idx, c_vals, p->path_rows,
+                                     (long long)p->host_st.rows_wide);
   return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 

@@ -46,7 +46,7 @@ struct DevStats {
   long long nruns_b;  // entries of its block-window-granular copy
   long long scratch_total;  // total of the transpose's prefix sum
   uint32_t err;
-  uint32_t pad;
+  uint32_t rows_wide;  // rows of the plan with more than 32 nonzeros of A
   int hist[NBINS];   // rows per bin
   int fill[NBINS];   // scatter cursors
   unsigned int work[8];  // dynamic work counters (reset before each use)
@@ -239,7 +239,8 @@ cudaError_t launch_numeric(const LaunchCtx& c, const Csr& A, const Csr& B, const
                            const PathBins& pb, const Tuning& tu, const SplitInfo& sp, int dtype,
                            const void* av, const void* bv, int32_t* cursor, int32_t* nxt,
                            const int32_t* c_rp, int32_t* c_ci, void* c_v,
-                           const int* path_rows /* host, may be null */);
+                           const int* path_rows /* host, may be null */,
+                           long long rows_wide /* rows with more than 32 nonzeros, -1: unknown */);
 
 cudaError_t launch_transpose(const LaunchCtx& c, long long m, long long n, long long nnz, const int32_t* rp,
                              const int32_t* ci, int32_t* t_rp, int32_t* t_ci, int32_t* t_src, int32_t* fill,

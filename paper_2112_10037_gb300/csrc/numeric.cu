@@ -34,7 +34,7 @@ static cudaError_t tiny_num(const LaunchCtx& c, const Csr& A, const Csr& B, cons
 template <typename T, int W>
 static cudaError_t warp_num(const LaunchCtx& c, const Csr& A, const Csr& B, const T* av, const T* bv,
                             const RowInfo& ri, int lo, int hi, const SplitInfo& sp, int32_t* cur, int32_t* nxt,
-                            const int32_t* c_rp, int32_t* c_ci, T* c_v) {
+                            const int32_t* c_rp, int32_t* c_ci, T* c_v, long long rows_wide) {
   auto k = k_num_warp<W, NUM_WARPS_CTA, T>;
   const size_t smem = (size_t)NUM_WARPS_CTA * ((size_t)W * sizeof(T) + W / 8);
   const int occ = kernel_blocks_per_sm(k, NUM_WARPS_CTA * 32, smem);
@@ -56,13 +56,16 @@ static cudaError_t warp_num(const LaunchCtx& c, const Csr& A, const Csr& B, cons
   const int occ1 = kernel_blocks_per_sm(k1, NW1 * 32, smem1);
   if (occ1 <= 0) return cudaErrorInvalidConfiguration;
   unsigned* counter1 = &c.st->work[3];
-  cudaError_t e = cudaMemsetAsync(ns.counter, 0, sizeof(unsigned), c.stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(counter1, 0, sizeof(unsigned), c.stream);
+  // the general kernel has work only for split rows and rows of more than
+  // 32 nonzeros (a stencil or Galerkin product has neither)
+  const bool general = rows_wide != 0 || (sp.heavy_bin < NBINS && sp.hcap > 0);
+  cudaError_t e = cudaMemsetAsync(counter1, 0, sizeof(unsigned), c.stream);
+  if (e == cudaSuccess && general) e = cudaMemsetAsync(ns.counter, 0, sizeof(unsigned), c.stream);
   if (e != cudaSuccess) return e;
   k1<<<c.nsm * occ1, NW1 * 32, smem1, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, ns, c_rp, c_ci, c_v,
                                                            counter1, c.err);
   count_launch(c);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaGetLastError()) != cudaSuccess || !general) return e;
   const int grid = c.nsm * occ;
   k<<<grid, NUM_WARPS_CTA * 32, smem, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, ns, cur, nxt, c_rp, c_ci, c_v,
                                                   c.err, 1);
@@ -110,7 +113,7 @@ template <typename T>
 static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
                              const PathBins& pb, const Tuning& tu, const SplitInfo& sp, const T* av,
                              const T* bv, int32_t* cur, int32_t* nxt, const int32_t* c_rp, int32_t* c_ci,
-                             T* c_v, const int* path_rows) {
+                             T* c_v, const int* path_rows, long long rows_wide) {
   cudaError_t e = cudaSuccess;
   if (pb.hi[PATH_TINY] >= pb.lo[PATH_TINY]) {
     const long long rows = rows_in(path_rows, PATH_TINY);
@@ -157,9 +160,9 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
   if (hi >= lo) {
     timer_mark(c, T_NUM_WARP, 0);
     switch (tu.window_warp) {
-      case 2048: e = warp_num<T, 2048>(c, A, B, av, bv, ri, lo, hi, sp, cur, nxt, c_rp, c_ci, c_v); break;
-      case 4096: e = warp_num<T, 4096>(c, A, B, av, bv, ri, lo, hi, sp, cur, nxt, c_rp, c_ci, c_v); break;
-      default: e = warp_num<T, 1024>(c, A, B, av, bv, ri, lo, hi, sp, cur, nxt, c_rp, c_ci, c_v); break;
+      case 2048: e = warp_num<T, 2048>(c, A, B, av, bv, ri, lo, hi, sp, cur, nxt, c_rp, c_ci, c_v, rows_wide); break;
+      case 4096: e = warp_num<T, 4096>(c, A, B, av, bv, ri, lo, hi, sp, cur, nxt, c_rp, c_ci, c_v, rows_wide); break;
+      default: e = warp_num<T, 1024>(c, A, B, av, bv, ri, lo, hi, sp, cur, nxt, c_rp, c_ci, c_v, rows_wide); break;
     }
     timer_mark(c, T_NUM_WARP, 1);
     if (e) return e;
@@ -170,12 +173,12 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
 cudaError_t launch_numeric(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
                            const PathBins& pb, const Tuning& tu, const SplitInfo& sp, int dtype,
                            const void* av, const void* bv, int32_t* cur, int32_t* nxt, const int32_t* c_rp,
-                           int32_t* c_ci, void* c_v, const int* path_rows) {
+                           int32_t* c_ci, void* c_v, const int* path_rows, long long rows_wide) {
   if (dtype == SPGEMM_F32)
     return numeric_t<float>(c, A, B, ri, pb, tu, sp, (const float*)av, (const float*)bv, cur, nxt, c_rp, c_ci,
-                            (float*)c_v, path_rows);
+                            (float*)c_v, path_rows, rows_wide);
   return numeric_t<double>(c, A, B, ri, pb, tu, sp, (const double*)av, (const double*)bv, cur, nxt, c_rp, c_ci,
-                           (double*)c_v, path_rows);
+                           (double*)c_v, path_rows, rows_wide);
 }
 
 }  // namespace sg
