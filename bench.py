@@ -40,9 +40,9 @@ from paper_2112_10037_gb300 import gen  # noqa: E402
 
 L2_BYTES = 129 * 1024 * 1024
 # default row classes of the library (register sort <= 128 products; numeric
-# warp window up to 32768 products, bins rounded to powers of two; block
+# warp window up to 65536 products, bins rounded to powers of two; block
 # window above)
-NUM_BLOCK_MIN = 32768
+NUM_BLOCK_MIN = 65536
 PEAKS_FILE = os.path.join(HERE, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -99,23 +99,33 @@ class ClockSampler:
         self.thread = None
 
     def start(self):
+        """Starts the sampler and waits (at most 5 s) for its first sample,
+        so that the timed region that follows is covered from its start."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except (OSError, FileNotFoundError):
             self.proc = None
             return
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        t_end = time.monotonic() + 5.0
+        while not self.lines and time.monotonic() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark(self):
+        """Host time of the start of the timed region."""
+        self.t0 = time.monotonic()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t1 = time.monotonic()
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -125,7 +135,9 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0 = getattr(self, "t0", None)
+        inside = [ln for t, ln in self.lines if t0 is None or t0 <= t <= t1 + 0.06]
+        for ln in inside:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -216,6 +228,7 @@ def run_ours(args, rank, world, A, B, desc):
         dist.barrier()
     sampler = ClockSampler(dev.index)
     sampler.start()
+    sampler.mark()
     times, ktimes, launches = [], [], 0
     for _ in range(args.steps):
         flush.fill_(1)                      # evict L2 between timed steps

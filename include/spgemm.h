@@ -95,7 +95,7 @@ typedef struct spgemm_opts {
   int32_t backward;    /* nonzero: the plan also keeps the transpose of A's structure,
                           which spgemm_backward needs (more workspace) */
   int32_t num_block_min;/* rows with more products than this run the numeric pass
-                          with a block-wide window (0: default 32768; -1: never, then
+                          with a block-wide window (0: default 65536; -1: never, then
                           heavy rows are split as split_min says) */
   int32_t block_warps; /* warps sharing a numeric block window (see window_block) */
   int32_t sort_max;    /* rows of at most this many products are merged by a sort in

@@ -29,7 +29,7 @@ DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "paper_2112_1003
 
 CANDIDATES = {
     "window_warp": [1024, 2048],
-    "num_block_min": [8192, 32768, 131072],
+    "num_block_min": [8192, 32768, 65536, 131072],
     "window_block": [4096, 8192],
     "block_warps": [8, 16],
     "warp_max": [8192],

@@ -112,7 +112,7 @@ int numeric_block_bin(const spgemm_opts& o) {
   if (o.force_path == 2) return tiny_hi_bin(o) + 1;                 // every row above the register sort
   if (o.force_path == 4) return 1;                                 // every non-empty row
   if (o.num_block_min < 0) return sg::NBINS;
-  const long long m = o.num_block_min > 0 ? o.num_block_min : 32768;
+  const long long m = o.num_block_min > 0 ? o.num_block_min : 65536;
   const int b = sg::bin_of(m) + 1;
   return b < tiny_hi_bin(o) + 1 ? tiny_hi_bin(o) + 1 : b;
 }

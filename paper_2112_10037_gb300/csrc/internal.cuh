@@ -163,6 +163,39 @@ __device__ __forceinline__ void red_add_shared(float* p, float v) {
   asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v) : "memory");
 }
 
+// acc += a * b on a shared-memory word, for FP64 as one fused multiply-add
+// under a compare-and-swap: GB300 runs FP64 at two lane-operations per SM per
+// clock, and a multiply followed by a shared-memory FP64 add costs two of
+// them; the swap itself runs on the shared-memory unit.  Equal addresses,
+// in one warp or in several, retry with the value that won.  Returns whether
+// the word still held +0.0, the cleared state, before this update: the first
+// update of a column sees it, so the caller marks the column present then
+// and skips the bitmap atomic on every later update.  FP32 adds in hardware
+// (red.shared.add.f32) and always reports a first update.
+constexpr int CAS_RETRY_LIMIT = 1 << 16;
+
+__device__ __forceinline__ bool is_cleared(double v) { return __double_as_longlong(v) == 0ll; }
+__device__ __forceinline__ bool is_cleared(float v) { return __float_as_uint(v) == 0u; }
+
+__device__ __forceinline__ bool fma_shared(double* p, double a, double b, uint32_t* err) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+  unsigned long long old;
+  asm volatile("ld.shared.u64 %0, [%1];" : "=l"(old) : "r"(s) : "memory");
+  for (int it = 0; it < CAS_RETRY_LIMIT; ++it) {
+    const unsigned long long nv = (unsigned long long)__double_as_longlong(fma(a, b, __longlong_as_double((long long)old)));
+    unsigned long long prev;
+    asm volatile("atom.shared.cas.b64 %0, [%1], %2, %3;" : "=l"(prev) : "r"(s), "l"(old), "l"(nv) : "memory");
+    if (prev == old) return old == 0ull;
+    old = prev;
+  }
+  atomicOr(err, EB_INTERNAL);  // never expected: each failed swap is another update's success
+  return false;
+}
+__device__ __forceinline__ bool fma_shared(float* p, float a, float b, uint32_t*) {
+  red_add_shared(p, a * b);
+  return true;
+}
+
 // Index of the first lane whose inclusive prefix `incl` exceeds p (incl is
 // non-decreasing over the 32 lanes).  Every lane must call it.
 __device__ __forceinline__ int warp_owner(int incl, int p) {

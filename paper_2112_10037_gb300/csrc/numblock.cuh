@@ -120,8 +120,7 @@ __device__ __forceinline__ void nb_range(const Csr& B, const T* __restrict__ bv,
       if (p0 + 32 * u + lane < hi) {
         const int j = cur.col[u] - base;
         if ((unsigned)j < (unsigned)W) {
-          atomicOr(&bits[j >> 5], 1u << (j & 31));
-          red_add_shared(&acc[j], cur.a[u] * cur.b[u]);
+          if (fma_shared(&acc[j], cur.a[u], cur.b[u], err)) atomicOr(&bits[j >> 5], 1u << (j & 31));
         } else {
           atomicOr(err, EB_UNSORTED);
         }

@@ -53,11 +53,14 @@ struct WarpWin {
   __device__ __forceinline__ void mark(int j) { atomicOr(&bits[j >> 5], 1u << (j & 31)); }
 
   // Lanes carry products of one segment: distinct columns, no claim needed.
+  // The column is marked present on its first update (the word still +0.0,
+  // its cleared state).
   __device__ __forceinline__ void add_distinct(int j, T a, T b, bool act) {
     if (act) {
       if ((unsigned)j < (unsigned)W) {
-        mark(j);
-        acc[j] = fma(a, b, acc[j]);
+        const T old = acc[j];
+        acc[j] = fma(a, b, old);
+        if (is_cleared(old)) mark(j);
       } else {
         atomicOr(err, EB_UNSORTED);
       }
@@ -66,7 +69,9 @@ struct WarpWin {
 
   // Lanes may carry equal columns (short segments of different B rows often
   // share the hub columns): shared-memory atomic add, which resolves equal
-  // addresses in hardware.
+  // addresses in hardware.  (The compare-and-swap of fma_shared saves an FP64
+  // operation per product, but its round trip lengthens this latency-bound
+  // loop: measured 7 % slower here.)
   __device__ __forceinline__ void add_atomic(int j, T a, T b, bool act) {
     if (act) {
       if ((unsigned)j < (unsigned)W) {
@@ -454,12 +459,14 @@ k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
   }
 }
 
-// Rows of at most 32 nonzeros of A (not split): one cursor per lane, and the
-// next window's short-segment products are placed and their loads issued
-// before this window is emitted, so the emission hides their latency.  Same
-// accumulator, emission and result as k_num_warp.
+// Rows of at most 32 nonzeros of A (not split): one cursor per lane.  Each
+// lane holds its current run and the next one, and loads the run after
+// that one window ahead, so the next window is known at the top of a
+// window: its short-segment products are placed and their loads issued
+// before this window's products are accumulated and emitted, which hide
+// their latency.  Same accumulator, emission and result as k_num_warp.
 template <int W, int NWARP, typename T>
-__global__ void __launch_bounds__(NWARP * 32)
+__global__ void __launch_bounds__(NWARP * 32, W <= 1024 ? 3 : 1)
 k_num_warp1(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri, const DevStats* st,
             int bin_lo, int bin_hi, NumSplit sp, const int32_t* __restrict__ c_rp, int32_t* __restrict__ c_ci,
             T* __restrict__ c_v, unsigned* counter, uint32_t* err) {
@@ -506,17 +513,25 @@ k_num_warp1(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
     int32_t* const rci = c_ci + rbeg;
     T* const rcv = c_v + rbeg;
     // this lane's nonzero: its current run (window wid, segment [s0, s1))
-    int rj = 0, wid = INT_MAX, s0 = 0, s1 = 0;
+    // and the next one (nwid, [ns0, ns1)); entries read past a row's
+    // sentinel are padding and never used
+    int rj = 0, wid = INT_MAX, s0 = 0, s1 = 0, nwid = INT_MAX, ns0 = 0, ns1 = 0;
     T a = T(0);
     const int e = a0 + lane;
     if (e < a1) {
       const int k = A.ci[e];
       a = av[e];
       rj = sp.rr[k];
-      const int2 c0 = sp.runs[rj];
-      wid = c0.x;
-      s0 = c0.y;
-      if (c0.x != INT_MAX) s1 = sp.runs[rj + 1].y;  // empty rows hold only the sentinel
+      const int2 c0 = sp.runs[rj], c1 = sp.runs[rj + 1];
+      const int y2 = sp.runs[rj + 2].y;
+      if (c0.x != INT_MAX) {  // empty rows hold only the sentinel
+        wid = c0.x;
+        s0 = c0.y;
+        s1 = c1.y;
+        nwid = c1.x;
+        ns0 = c1.y;
+        ns1 = y2;
+      }
     }
     int w = warp_min(wid);
     typename WarpWin<W, T>::Flat f;
@@ -525,26 +540,34 @@ k_num_warp1(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
     while (w != INT_MAX) {
       const int base = w << WSHIFT;
       const bool act = wid == w;
-      // loads of this lane's next run, for the advance below
-      int2 nx = make_int2(wid, s0);
-      int nend = s1;
-      if (act) {
-        nx = sp.runs[rj + 1];
-        if (nx.x != INT_MAX) nend = sp.runs[rj + 2].y;
+      // the run after the next one, for the window after the next
+      int2 n2 = make_int2(INT_MAX, 0);
+      int n2end = 0;
+      if (act && nwid != INT_MAX) {
+        n2 = sp.runs[rj + 2];
+        n2end = sp.runs[rj + 3].y;
       }
+      // the next window and its short-segment products, their loads in
+      // flight while this window is accumulated and emitted
+      const int wid1 = act ? nwid : wid, s01 = act ? ns0 : s0, s11 = act ? ns1 : s1;
+      const int wn = warp_min(wid1);
+      typename WarpWin<W, T>::Flat fn;
+      if (wn != INT_MAX) win.flat_gather(B, bv, s01, wid1 == wn ? s11 - s01 : 0, a, wn << WSHIFT, fn);
       const int len = act ? s1 - s0 : 0;
       win.long_segments(B, bv, s0, len, a, base);
       win.flat_apply(B, bv, s0, a, base, f);
-      if (act) {
-        ++rj;
-        wid = nx.x;
-        s0 = nx.y;
-        s1 = nend;
-      }
-      const int wn = warp_min(wid);
-      if (wn != INT_MAX) win.flat_gather(B, bv, s0, wid == wn ? s1 - s0 : 0, a, wn << WSHIFT, f);
       const int ncols = min(W, cmx - base + 1);
       out += win.emit(base, ncols, out, out_end, rci, rcv);
+      if (act) {
+        ++rj;
+        wid = nwid;
+        s0 = ns0;
+        s1 = ns1;
+        nwid = n2.x;
+        ns0 = n2.y;
+        ns1 = n2end;
+      }
+      f = fn;
       w = wn;
     }
     if (lane == 0 && out != out_end) atomicOr(err, EB_INTERNAL);

@@ -57,7 +57,7 @@ def _sample_rows(prod, rng):
     order = np.argsort(prod, kind="stable")
     nz = order[prod[order] > 0]
     pick = [nz[-16:]]  # the heaviest rows (block window)
-    for edge in (128, 8192, 32768):  # both sides of each path boundary
+    for edge in (128, 8192, 32768, 65536):  # both sides of each path boundary
         i = np.searchsorted(prod[nz], edge)
         pick.append(nz[max(0, i - 8):i + 8])
     pick.append(rng.choice(nz, 64, replace=False))
