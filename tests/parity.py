@@ -48,3 +48,31 @@ def assert_values_close(got_vals, ref_vals, scale, rtol=RTOL_F64):
 
 def assert_values_exact(got_vals, ref_vals):
     assert np.array_equal(np.asarray(got_vals, np.float64), np.asarray(ref_vals, np.float64))
+
+
+def load_golden(path):
+    """Matrices of a text fixture under tests/golden/ (format in the file's
+    header): {name: CSR}."""
+    mats, cur = {}, None
+    with open(path) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            if line.startswith("matrix "):
+                _, name, m, n = line.split()
+                cur = {"name": name, "m": int(m), "n": int(n), "rows": []}
+                mats[name] = cur
+                continue
+            head, _, rest = line.partition(":")
+            assert head.split()[0] == "row" and int(head.split()[1]) == len(cur["rows"]), line
+            cur["rows"].append([(int(c), float(v)) for c, v in (t.split(":") for t in rest.split())])
+    out = {}
+    for name, d in mats.items():
+        assert len(d["rows"]) == d["m"], name
+        rp = np.zeros(d["m"] + 1, np.int32)
+        rp[1:] = np.cumsum([len(r) for r in d["rows"]])
+        ci = np.array([c for r in d["rows"] for c, _ in r], np.int32)
+        v = np.array([x for r in d["rows"] for _, x in r], np.float64)
+        out[name] = gen.CSR(d["m"], d["n"], rp, ci, v)
+    return out

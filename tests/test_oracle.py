@@ -8,6 +8,8 @@ product or wrong index (brute force, closed forms), a transposed operand
 repeated output columns (structure checks), a lost pattern entry on
 cancellation (explicit-zero test).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -307,3 +309,24 @@ def test_backward_finite_differences(oracle_mod):
         B2.vals[q] += h
         fd = (_loss(oracle_mod, A, B2, W_of) - L0) / h
         assert abs(fd - db[q]) <= 1e-9 * (1 + abs(db[q]))
+
+
+# ------------------------------------------------------- hand-worked example
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "gustavson_worked_example.txt")
+
+
+def test_golden_worked_example(oracle_mod):
+    """The oracle against a product worked out by hand from the row-wise
+    Gustavson definition (Sec. 2.2): exact structure (a cancelled entry
+    stays, an empty row, an A entry whose B row is empty) and exact values,
+    and the gradient of the sum of C's entries."""
+    from parity import load_golden
+    g = load_golden(GOLDEN)
+    A, B, Cref = g["A"], g["B"], g["C"]
+    C = oracle_mod.spgemm(A, B)
+    assert np.array_equal(np.asarray(C.row_ptr, np.int64), np.asarray(Cref.row_ptr, np.int64))
+    assert np.array_equal(C.col_idx, Cref.col_idx)
+    assert np.array_equal(C.vals, Cref.vals)
+    da, db = oracle_mod.backward(A, B, C.row_ptr, C.col_idx, np.ones(C.nnz))
+    assert np.array_equal(da, g["dA"].vals) and np.array_equal(g["dA"].col_idx, A.col_idx)
+    assert np.array_equal(db, g["dB"].vals) and np.array_equal(g["dB"].col_idx, B.col_idx)
