@@ -39,9 +39,11 @@ sys.path.insert(0, HERE)
 from paper_2112_10037_gb300 import gen  # noqa: E402
 
 L2_BYTES = 129 * 1024 * 1024
-# default row classes of the library (register sort <= 128 products; numeric
-# warp window up to 65536 products, bins rounded to powers of two; block
-# window above)
+# default row classes of the library (register sort <= 16 products, hash
+# accumulator 17..128; numeric warp window up to 65536 products, bins rounded
+# to powers of two; block window above)
+TINY_MAX = 16
+HASH_MAX = 128
 NUM_BLOCK_MIN = 65536
 PEAKS_FILE = os.path.join(HERE, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -208,6 +210,8 @@ def run_ours(args, rank, world, A, B, desc):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
 
     kw = {} if world == 1 else {"row_range": (rb, re)}
+    if args.hash_max:
+        kw["hash_max"] = args.hash_max
 
     def step(profile=False):
         plan = api.Plan(dA, dB, dtype=torch.float64, **kw)
@@ -294,6 +298,7 @@ def run_ours(args, rank, world, A, B, desc):
         "higher_is_better": True, "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic (seeded generator, no dataset)",
         "config": dict(desc, products=int(prod.sum()), nnz_C=nnz_c, l2="flushed between timed steps",
+                       **({"hash_max": args.hash_max} if args.hash_max else {}),
                        parallelism="row blocks balanced by products" if world > 1 else "single GPU"),
         "kernel_ms": {n: round(avg[n], 4) for n in names},
         "rows_per_path": dict(zip(["tiny", "hash", "warp", "block"], plan_stats[2])),
@@ -310,13 +315,15 @@ def kernel_bytes(A, B, prod_rows, c_rp, kernel, row_begin):
     kernel's rows."""
     P = np.asarray(prod_rows, np.int64)
     path = kernel.split("_", 1)[1]
-    # register sort up to 128 products; every larger row runs in the warp
-    # window kernel (numeric) / the bitmap kernels (symbolic warp <= 8192 < block)
+    # register sort up to 16 products, hash accumulator up to 128; every
+    # larger row runs in the warp window kernel (numeric) / the bitmap
+    # kernels (symbolic warp <= 8192 < block)
+    small = {"tiny": (1, TINY_MAX), "hash": (TINY_MAX + 1, HASH_MAX)}
     if kernel.startswith("num"):
-        lo, hi = {"tiny": (1, 128), "warp": (129, NUM_BLOCK_MIN), "block": (NUM_BLOCK_MIN + 1, 1 << 62)}.get(
+        lo, hi = dict(small, warp=(HASH_MAX + 1, NUM_BLOCK_MIN), block=(NUM_BLOCK_MIN + 1, 1 << 62)).get(
             path, (0, -1))
     else:
-        lo, hi = {"tiny": (1, 128), "warp": (129, 8192), "block": (8193, 1 << 62)}.get(path, (0, -1))
+        lo, hi = dict(small, warp=(HASH_MAX + 1, 8192), block=(8193, 1 << 62)).get(path, (0, -1))
     rows = np.flatnonzero((P >= lo) & (P <= hi))
     if len(rows) == 0:
         return 0.0
@@ -340,9 +347,11 @@ def kernel_products(prod_rows, kernel):
     """Products handled by the numeric kernel of this path (host bookkeeping)."""
     P = np.asarray(prod_rows, np.int64)
     if kernel == "num_tiny":
-        return int(P[(P >= 1) & (P <= 128)].sum())
+        return int(P[(P >= 1) & (P <= TINY_MAX)].sum())
+    if kernel == "num_hash":
+        return int(P[(P > TINY_MAX) & (P <= HASH_MAX)].sum())
     if kernel == "num_warp":
-        return int(P[(P > 128) & (P <= NUM_BLOCK_MIN)].sum())
+        return int(P[(P > HASH_MAX) & (P <= NUM_BLOCK_MIN)].sum())
     return int(P[P > NUM_BLOCK_MIN].sum())
 
 
@@ -645,6 +654,8 @@ def main():
     ap.add_argument("--e2e-streams", type=int, default=1, help="compute streams of the end-to-end leg")
     ap.add_argument("--e2e-order", default="rows", choices=["products", "rows"],
                     help="order of the end-to-end leg's row ranges")
+    ap.add_argument("--hash-max", type=int, default=0,
+                    help="largest row product count of the hash accumulator (0: library default 128, -1: off)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -49,7 +49,9 @@ typedef enum spgemm_status {
   SPGEMM_ERR_UNSORTED_INPUT = 3,  /* a column index out of range, repeated or descending */
   SPGEMM_ERR_INDEX_OVERFLOW = 4,  /* nnz(C) (or an input nnz) does not fit int32 */
   SPGEMM_ERR_WORKSPACE = 5,       /* workspace NULL or smaller than spgemm_workspace_size */
-  SPGEMM_ERR_TABLE_OVERFLOW = 6,  /* reserved: not returned by this version */
+  SPGEMM_ERR_TABLE_OVERFLOW = 6,  /* a shared-memory hash table found no free slot (the
+                                     tables are sized at twice a row's products, so this
+                                     means broken input or a library fault) */
   SPGEMM_ERR_CUDA = 7,            /* a CUDA runtime call failed */
   SPGEMM_ERR_INTERNAL = 8,
   SPGEMM_ERR_NOT_READY = 9        /* calls out of order (numeric before symbolic) */
@@ -80,8 +82,12 @@ typedef struct spgemm_opts {
   int32_t force_path;  /* -1: automatic.  Testing overrides: 1 (2) sends every row
                           above the register-sort limit to the warp (block) path;
                           3 (4) sends every non-empty row to the warp (block) path */
-  int32_t hash_max;    /* reserved, ignored: there is no hash accumulator (register
-                          sorts and dense column windows cover every row size) */
+  int32_t hash_max;    /* rows of 17 .. hash_max products use the warp hash accumulator
+                          (a shared-memory table of twice the row's products, ranked
+                          into column order); 0: 128, otherwise rounded up to 32, 64 or
+                          128; -1: off (register sort up to sort_max).  Off as well when
+                          force_path >= 0 or sort_max is 256 or 512.  Rows of at most
+                          16 products always use the register sort */
   int32_t window_warp; /* columns of the numeric dense window (one per warp):
                           1024, 2048 or 4096 (0: default 1024) */
   int32_t window_block;/* columns of the numeric block window, with block_warps one of
@@ -99,7 +105,9 @@ typedef struct spgemm_opts {
                           heavy rows are split as split_min says) */
   int32_t block_warps; /* warps sharing a numeric block window (see window_block) */
   int32_t sort_max;    /* rows of at most this many products are merged by a sort in
-                          registers: 128, 256 or 512 (0: 128) */
+                          registers: 128, 256 or 512 (0: 128); rows of 17 or more
+                          products take the hash path instead unless it is off
+                          (see hash_max) */
   int32_t reserved[2];
 } spgemm_opts;
 
@@ -181,7 +189,7 @@ spgemm_status spgemm_numeric(spgemm_plan* plan, const void* a_vals, const void* 
 
 /* Work statistics of an analysed plan (blocks on `stream` to read them):
  * total and largest per-row product count, and the number of rows sent to
- * the register-sort, hash (always 0: no such path), warp and block paths of
+ * the register-sort, hash, warp and block paths of
  * the symbolic pass.  Any output may be NULL. */
 spgemm_status spgemm_plan_stats(spgemm_plan* plan, spgemm_stream_t stream,
                                 int64_t* total_products, int64_t* max_row_products,
@@ -194,8 +202,8 @@ spgemm_status spgemm_plan_stats(spgemm_plan* plan, spgemm_stream_t stream,
  * in ms[0..n-1], in this order: analyse, symbolic register-sort, symbolic
  * hash, symbolic warp, symbolic block, scan, numeric register-sort, numeric
  * hash, numeric warp, numeric block (SPGEMM_TIMER_COUNT entries; groups
- * never run, such as the two hash groups, read as 0).  Creating the events is the only resource this
- * allocates (host-side event handles). */
+ * the plan never ran read as 0).  Creating the events is the only resource
+ * this allocates (host-side event handles). */
 #define SPGEMM_TIMER_COUNT 10
 spgemm_status spgemm_plan_set_profiling(spgemm_plan* plan, int on);
 spgemm_status spgemm_plan_kernel_times(spgemm_plan* plan, float* ms, int n);

@@ -64,7 +64,7 @@ def _stream_handle(stream=None) -> int:
 
 def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1, warp_max=0,
               window_warp=0, window_block=0, split_min=0, backward=False, num_block_min=0,
-              block_warps=0, sort_max=0) -> nat.spgemm_opts:
+              block_warps=0, sort_max=0, hash_max=0) -> nat.spgemm_opts:
     o = nat.spgemm_opts_default()
     o.dtype = _DT[dtype]
     o.validate = 1 if validate else 0
@@ -79,6 +79,7 @@ def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1
     o.num_block_min = int(num_block_min)
     o.block_warps = int(block_warps)
     o.sort_max = int(sort_max)
+    o.hash_max = int(hash_max)
     return o
 
 
@@ -156,7 +157,7 @@ class Plan:
 
     def stats(self):
         """(total products, largest row's products, rows per path
-        [register-sort, hash (always 0), warp, block] of the symbolic pass)."""
+        [register-sort, hash, warp, block] of the symbolic pass)."""
         return nat.spgemm_plan_stats(self.handle, self.stream)
 
     def check(self):

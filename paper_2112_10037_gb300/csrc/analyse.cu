@@ -31,12 +31,51 @@ __global__ void k_validate(Csr M, uint32_t* err) {
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, EB_UNSORTED);
 }
 
-// One warp per row of A: P_i, the smallest and largest column any product
-// of the row reaches (first and last column of each touched B row, since B's
-// rows are sorted), histogram of bins, total and maximum P.
+// Sum, minimum and maximum over aligned groups of G lanes (every lane of the
+// warp calls them; G = 32 uses the single-instruction warp reductions).
+template <int G, typename V>
+__device__ __forceinline__ V group_sum(V v) {
+  if constexpr (G == 32) {
+    return warp_sum(v);
+  } else {
+#pragma unroll
+    for (int d = G / 2; d >= 1; d >>= 1) v += __shfl_xor_sync(FULL, v, d);
+    return v;
+  }
+}
+template <int G>
+__device__ __forceinline__ int group_min(int v) {
+  if constexpr (G == 32) {
+    return warp_min(v);
+  } else {
+#pragma unroll
+    for (int d = G / 2; d >= 1; d >>= 1) v = min(v, __shfl_xor_sync(FULL, v, d));
+    return v;
+  }
+}
+template <int G>
+__device__ __forceinline__ int group_max(int v) {
+  if constexpr (G == 32) {
+    return warp_max(v);
+  } else {
+#pragma unroll
+    for (int d = G / 2; d >= 1; d >>= 1) v = max(v, __shfl_xor_sync(FULL, v, d));
+    return v;
+  }
+}
+
+// G lanes per row of A (32: one warp; 8: four rows per warp, for matrices
+// of short rows, where a warp per row leaves most lanes idle and each
+// warp's rows form one long chain of dependent loads): P_i, the smallest and
+// largest column any product of the row reaches (first and last column of
+// each touched B row, since B's rows are sorted), histogram of bins, total
+// and maximum P.
+template <int G>
 __global__ void __launch_bounds__(256) k_analyse(Csr A, Csr B, long long row_begin, long long mloc,
                                                  long long* __restrict__ prod, int* __restrict__ cmin,
                                                  int* __restrict__ cmax, DevStats* st) {
+  static_assert(G == 8 || G == 16 || G == 32, "lanes per row");
+  constexpr int RPW = 32 / G;  // rows per warp step
   __shared__ int s_hist[NBINS];
   __shared__ unsigned long long s_total, s_max;
   __shared__ unsigned s_wide;
@@ -44,28 +83,35 @@ __global__ void __launch_bounds__(256) k_analyse(Csr A, Csr B, long long row_beg
   if (threadIdx.x == 0) { s_total = 0; s_max = 0; s_wide = 0; }
   if (block_skip(st)) return;  // validated input was rejected
   const int lane = lane_id();
+  const int gl = lane & (G - 1), g = lane / G;
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
   unsigned long long my_total = 0, my_max = 0;
   unsigned my_wide = 0;
   bool bad = false;
-  for (long long r = w; r < mloc; r += nw) {
+  for (long long r0 = w * RPW; r0 < mloc; r0 += nw * RPW) {
+    const long long r = r0 + g;
+    const bool vr = r < mloc;
     const long long i = row_begin + r;
-    const int a0 = A.rp[i], a1 = A.rp[i + 1];
+    int a0 = 0, a1 = 0;
+    if (vr) {
+      a0 = A.rp[i];
+      a1 = A.rp[i + 1];
+    }
     long long p = 0;
     int mn = INT_MAX, mx = -1;
     // four entries per lane per step, their dependent loads in flight
     // together (long rows of power-law matrices otherwise form the tail)
-    for (int e0 = a0 + lane; e0 < a1; e0 += 128) {
+    for (int e0 = a0 + gl; e0 < a1; e0 += 4 * G) {
       int kk[4], ss[4], tt[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int e = e0 + 32 * u;
+        const int e = e0 + G * u;
         kk[u] = e < a1 ? A.ci[e] : -1;
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int e = e0 + 32 * u;
+        const int e = e0 + G * u;
         ss[u] = tt[u] = 0;
         if (e < a1) {
           if (kk[u] < 0 || (long long)kk[u] >= B.nrows) {
@@ -85,10 +131,10 @@ __global__ void __launch_bounds__(256) k_analyse(Csr A, Csr B, long long row_beg
         }
       }
     }
-    p = warp_sum(p);
-    mn = warp_min(mn);
-    mx = warp_max(mx);
-    if (lane == 0) {
+    p = group_sum<G>(p);
+    mn = group_min<G>(mn);
+    mx = group_max<G>(mx);
+    if (vr && gl == 0) {
       my_wide += a1 - a0 > 32 ? 1u : 0u;
       prod[r] = p;
       cmin[r] = mn;
@@ -98,11 +144,11 @@ __global__ void __launch_bounds__(256) k_analyse(Csr A, Csr B, long long row_beg
       my_max = my_max > (unsigned long long)p ? my_max : (unsigned long long)p;
     }
   }
-  if (lane == 0 && my_total) {
+  if (gl == 0 && my_total) {
     atomicAdd(&s_total, my_total);
     atomicMax(&s_max, my_max);
   }
-  if (lane == 0 && my_wide) atomicAdd(&s_wide, my_wide);
+  if (gl == 0 && my_wide) atomicAdd(&s_wide, my_wide);
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(&st->err, EB_UNSORTED);
   __syncthreads();
   if (threadIdx.x < NBINS && s_hist[threadIdx.x]) atomicAdd(&st->hist[threadIdx.x], s_hist[threadIdx.x]);
@@ -152,15 +198,38 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const long long* __restrict
 
 static int grid_for_warps(long long nwarps, int warps_per_block, int nsm);
 
+// True (for the whole block) when win_lo > 0 and the analysis put no row in
+// bins win_lo and above, i.e. no row takes a numeric window path and the
+// window-run lists will never be read.
+__device__ __forceinline__ bool no_window_rows(const DevStats* st, int win_lo) {
+  __shared__ int s_none;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int b = win_lo > 0 ? win_lo : NBINS; b < NBINS; ++b) n += st->hist[b];
+    s_none = win_lo > 0 && n == 0;
+  }
+  __syncthreads();
+  return s_none != 0;
+}
+
 // Window-run lists of B (see SplitInfo), at two window widths (shifts s1
 // and s2) from one read of B: pass 1 counts the runs of each row (plus its
 // sentinel), an exclusive scan turns counts into run pointers, pass 2 writes
 // (window id, first position) of every run.  One warp per row; a run starts
 // where the window id differs from the previous entry's.  A null second list
-// is skipped.
+// is skipped.  With no row in a window bin (win_lo, see no_window_rows) the
+// counts are written as zeros and the lists stay unbuilt.
 __global__ void __launch_bounds__(256) k_runs_count(Csr B, int s1, int32_t* __restrict__ rr1, int s2,
-                                                    int32_t* __restrict__ rr2, const DevStats* st) {
+                                                    int32_t* __restrict__ rr2, const DevStats* st, int win_lo) {
   if (block_skip(st)) return;
+  if (no_window_rows(st, win_lo)) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < B.nrows;
+         k += (long long)gridDim.x * blockDim.x) {
+      rr1[k] = 0;
+      if (rr2) rr2[k] = 0;
+    }
+    return;
+  }
   const int lane = lane_id();
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
@@ -220,8 +289,9 @@ __device__ __forceinline__ void runs_fill_row(const Csr& B, int k, int shift, co
 
 __global__ void __launch_bounds__(256) k_runs_fill(Csr B, int s1, const int32_t* __restrict__ rr1,
                                                    int2* __restrict__ runs1, int s2, const int32_t* __restrict__ rr2,
-                                                   int2* __restrict__ runs2, const DevStats* st) {
+                                                   int2* __restrict__ runs2, const DevStats* st, int win_lo) {
   if (block_skip(st)) return;
+  if (no_window_rows(st, win_lo)) return;
   const long long w = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
   for (long long k = w; k < B.nrows; k += nw) {
@@ -230,7 +300,7 @@ __global__ void __launch_bounds__(256) k_runs_fill(Csr B, int s1, const int32_t*
   }
 }
 
-cudaError_t launch_runs(const LaunchCtx& c, const Csr& B, const SplitInfo& sp, long long* partials) {
+cudaError_t launch_runs(const LaunchCtx& c, const Csr& B, const SplitInfo& sp, long long* partials, int win_lo) {
   if (!sp.rr || !sp.runs) return cudaSuccess;
   const bool two = sp.rrb && sp.runsb;
   if (B.nrows <= 0) {
@@ -239,7 +309,8 @@ cudaError_t launch_runs(const LaunchCtx& c, const Csr& B, const SplitInfo& sp, l
     return e;
   }
   const int grid = grid_for_warps(B.nrows, 8, c.nsm);
-  k_runs_count<<<grid, 256, 0, c.stream>>>(B, sp.wf_shift, sp.rr, sp.wb_shift, two ? sp.rrb : nullptr, c.st);
+  k_runs_count<<<grid, 256, 0, c.stream>>>(B, sp.wf_shift, sp.rr, sp.wb_shift, two ? sp.rrb : nullptr, c.st,
+                                           win_lo);
   count_launch(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -247,7 +318,7 @@ cudaError_t launch_runs(const LaunchCtx& c, const Csr& B, const SplitInfo& sp, l
   if (e == cudaSuccess && two) e = launch_scan(c, sp.rrb, B.nrows, partials, &c.st->nruns_b);
   if (e != cudaSuccess) return e;
   k_runs_fill<<<grid, 256, 0, c.stream>>>(B, sp.wf_shift, sp.rr, sp.runs, sp.wb_shift, two ? sp.rrb : nullptr,
-                                          two ? sp.runsb : nullptr, c.st);
+                                          two ? sp.runsb : nullptr, c.st, win_lo);
   count_launch(c);
   return cudaGetLastError();
 }
@@ -269,8 +340,13 @@ cudaError_t launch_analyse(const LaunchCtx& c, const Csr& A, const Csr& B, long 
                            long long mloc, long long* prod, int* cmin, int* cmax, int* rows) {
   if (mloc <= 0) return cudaSuccess;
   timer_mark(c, T_ANALYSE, 0);
-  k_analyse<<<grid_for_warps(mloc, 8, c.nsm), 256, 0, c.stream>>>(A, B, row_begin, mloc, prod, cmin,
-                                                                   cmax, c.st);
+  // short rows on average (stencils, aggregation operators): 8 lanes per row
+  if (A.nrows > 0 && A.nnz <= 12 * A.nrows)
+    k_analyse<8><<<grid_for_warps((mloc + 3) / 4, 8, c.nsm), 256, 0, c.stream>>>(A, B, row_begin, mloc, prod,
+                                                                                 cmin, cmax, c.st);
+  else
+    k_analyse<32><<<grid_for_warps(mloc, 8, c.nsm), 256, 0, c.stream>>>(A, B, row_begin, mloc, prod, cmin,
+                                                                       cmax, c.st);
   count_launch(c);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -78,6 +78,28 @@ int tiny_hi_bin(const spgemm_opts& o) {
   return m >= 512 ? 10 : (m >= 256 ? 9 : 8);
 }
 
+// First bin of the hash path (rows of 17 or more products; smaller rows keep
+// the register sort, whose network is then at most 16 elements wide).
+constexpr int HASH_LO_BIN = 6;
+
+// Last bin of the hash path, 0 when it is off: rows of 17..opts.hash_max
+// products (0: 128; rounded up to 32, 64 or 128).  Off with hash_max < 0,
+// with a forced path, or when a register sort above 128 products is asked
+// for (sort_max 256 or 512).
+int hash_hi_bin(const spgemm_opts& o) {
+  if (o.hash_max < 0 || o.force_path >= 0 || o.sort_max > 128) return 0;
+  int m = o.hash_max > 0 ? o.hash_max : 128;
+  if (m < 17) m = 17;
+  if (m > 128) m = 128;
+  return sg::bin_of(m);
+}
+
+// Last bin of the rows that need no column window (register sort or hash).
+int small_hi_bin(const spgemm_opts& o) {
+  const int h = hash_hi_bin(o);
+  return h > 0 ? h : tiny_hi_bin(o);
+}
+
 // Window geometry and split capacity from the options and B's width (see
 // sg::SplitInfo).  *hcnt_entries is 0 when no row is split.
 void split_geometry(const spgemm_opts& o, int window, long long mloc, long long ncols_b, sg::SplitInfo* sp,
@@ -100,7 +122,7 @@ void split_geometry(const spgemm_opts& o, int window, long long mloc, long long 
   // split rows always lie above the register-sort bins (1..8), so their
   // sizes come from the bitmap-window kernel, which records per-window counts
   sp->heavy_bin = sg::bin_of(smin) + 1;
-  if (sp->heavy_bin < tiny_hi_bin(o) + 1) sp->heavy_bin = tiny_hi_bin(o) + 1;
+  if (sp->heavy_bin < small_hi_bin(o) + 1) sp->heavy_bin = small_hi_bin(o) + 1;
   if (sp->heavy_bin >= sg::NBINS) { sp->heavy_bin = sg::NBINS; return; }
   sp->hcap = (int)cap;
   *hcnt_entries = (size_t)cap * (size_t)sp->ntf;
@@ -114,7 +136,7 @@ int numeric_block_bin(const spgemm_opts& o) {
   if (o.num_block_min < 0) return sg::NBINS;
   const long long m = o.num_block_min > 0 ? o.num_block_min : 65536;
   const int b = sg::bin_of(m) + 1;
-  return b < tiny_hi_bin(o) + 1 ? tiny_hi_bin(o) + 1 : b;
+  return b < small_hi_bin(o) + 1 ? small_hi_bin(o) + 1 : b;
 }
 
 int numeric_window(const spgemm_opts& o) {
@@ -204,10 +226,12 @@ void choose_paths(const spgemm_opts& o, sg::PathBins* pb, sg::Tuning* tu) {
   tu->warp_max = o.warp_max > 0 ? o.warp_max : 8192;
   tu->window_warp = numeric_window(o);
   block_geometry(o, &tu->window_block, &tu->block_warps);
-  tu->hash_max = 0;
+  const int HASH_HI = hash_hi_bin(o);
+  tu->hash_max = HASH_HI > 0 ? 1 << (HASH_HI - 1) : 0;
   tu->num_lo_block = numeric_block_bin(o);
   const int TINY_HI = tiny_hi_bin(o);  // register sort up to opts.sort_max products
-  const int wb = sg::bin_of(tu->warp_max) < TINY_HI + 1 ? TINY_HI + 1 : sg::bin_of(tu->warp_max);
+  const int SMALL_HI = small_hi_bin(o);
+  const int wb = sg::bin_of(tu->warp_max) < SMALL_HI + 1 ? SMALL_HI + 1 : sg::bin_of(tu->warp_max);
   for (int p = 0; p < sg::NPATHS; ++p) { pb->lo[p] = 1; pb->hi[p] = 0; }
   switch (o.force_path) {
     case 1: pb->lo[sg::PATH_TINY] = 1; pb->hi[sg::PATH_TINY] = TINY_HI; pb->lo[sg::PATH_WARP] = TINY_HI + 1; pb->hi[sg::PATH_WARP] = last; break;
@@ -215,8 +239,9 @@ void choose_paths(const spgemm_opts& o, sg::PathBins* pb, sg::Tuning* tu) {
     case 3: pb->lo[sg::PATH_WARP] = 1; pb->hi[sg::PATH_WARP] = last; break;
     case 4: pb->lo[sg::PATH_BLOCK] = 1; pb->hi[sg::PATH_BLOCK] = last; break;
     default:
-      pb->lo[sg::PATH_TINY] = 1; pb->hi[sg::PATH_TINY] = TINY_HI;
-      pb->lo[sg::PATH_WARP] = TINY_HI + 1; pb->hi[sg::PATH_WARP] = wb;
+      pb->lo[sg::PATH_TINY] = 1; pb->hi[sg::PATH_TINY] = HASH_HI > 0 ? HASH_LO_BIN - 1 : TINY_HI;
+      if (HASH_HI > 0) { pb->lo[sg::PATH_HASH] = HASH_LO_BIN; pb->hi[sg::PATH_HASH] = HASH_HI; }
+      pb->lo[sg::PATH_WARP] = SMALL_HI + 1; pb->hi[sg::PATH_WARP] = wb;
       pb->lo[sg::PATH_BLOCK] = wb + 1; pb->hi[sg::PATH_BLOCK] = last;
       break;
   }
@@ -338,7 +363,16 @@ static spgemm_status analyse_impl(const spgemm_csr* A, const spgemm_csr* B, cons
     if (e == cudaSuccess) e = sg::launch_validate(c, p->B);
   }
   if (e == cudaSuccess) e = sg::launch_analyse(c, p->A, p->B, p->row_begin, p->mloc, p->prod, p->cmin, p->cmax, p->rows);
-  if (e == cudaSuccess && !base) e = sg::launch_runs(c, p->B, p->sp, p->runs_part);
+  if (e == cudaSuccess && !base) {
+    // Only the numeric window paths read the run lists.  A plan of every row
+    // of A may leave them unbuilt when none of its rows takes such a path:
+    // plans derived from it cover subsets of those rows.
+    int win_lo = sg::NBINS;
+    for (int q : {sg::PATH_WARP, sg::PATH_BLOCK})
+      if (p->pb.hi[q] >= p->pb.lo[q] && p->pb.lo[q] < win_lo) win_lo = p->pb.lo[q];
+    if (rb != 0 || re != A->nrows) win_lo = 0;
+    e = sg::launch_runs(c, p->B, p->sp, p->runs_part, win_lo);
+  }
   if (e == cudaSuccess && o.backward) {
     p->at_rp = (int32_t*)(p->ws + L.at_rp);
     p->at_ci = (int32_t*)(p->ws + L.at_ci);
@@ -493,7 +527,7 @@ spgemm_status spgemm_numeric(spgemm_plan* p, const void* a_vals, const void* b_v
   const sg::RowInfo ri = rowinfo_of(p);
   cudaError_t e = sg::launch_numeric(c, p->A, p->B, ri, p->pb, p->tu, p->sp, p->opts.dtype, a_vals, b_vals,
                                      p->cursor, p->nxt, c_row_ptr, c_col_idx, c_vals, p->path_rows,
-                                     (long long)p->host_st.rows_wide);
+                                     (long long)p->host_st.rows_wide, p->host_st.hist);
   return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 

@@ -261,7 +261,10 @@ inline void count_launch(const LaunchCtx& c) {
 cudaError_t launch_validate(const LaunchCtx& c, const Csr& M);
 cudaError_t launch_analyse(const LaunchCtx& c, const Csr& A, const Csr& B, long long row_begin,
                            long long mloc, long long* prod, int* cmin, int* cmax, int* rows);
-cudaError_t launch_runs(const LaunchCtx& c, const Csr& B, const SplitInfo& sp, long long* partials);
+// win_lo > 0: skip building the lists when the analysis put no row in bins
+// win_lo and above (only valid when no other plan reads this plan's lists
+// for rows outside it).
+cudaError_t launch_runs(const LaunchCtx& c, const Csr& B, const SplitInfo& sp, long long* partials, int win_lo);
 cudaError_t launch_symbolic(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
                             const PathBins& pb, const Tuning& tu, const SplitInfo& sp, int32_t* cursor,
                             int32_t* c_rp, const int* path_rows /* host, may be null */);
@@ -273,7 +276,9 @@ cudaError_t launch_numeric(const LaunchCtx& c, const Csr& A, const Csr& B, const
                            const void* av, const void* bv, int32_t* cursor, int32_t* nxt,
                            const int32_t* c_rp, int32_t* c_ci, void* c_v,
                            const int* path_rows /* host, may be null */,
-                           long long rows_wide /* rows with more than 32 nonzeros, -1: unknown */);
+                           long long rows_wide /* rows with more than 32 nonzeros, -1: unknown */,
+                           const int* hist /* host rows per bin, may be null: bins without rows
+                                              are not launched */);
 
 cudaError_t launch_transpose(const LaunchCtx& c, long long m, long long n, long long nnz, const int32_t* rp,
                              const int32_t* ci, int32_t* t_rp, int32_t* t_ci, int32_t* t_src, int32_t* fill,

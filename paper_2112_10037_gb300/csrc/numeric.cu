@@ -4,6 +4,7 @@
 #include "launch_util.cuh"
 #include "numblock.cuh"
 #include "numwarp.cuh"
+#include "rowhash.cuh"
 #include "rowpass.cuh"
 
 namespace sg {
@@ -29,6 +30,41 @@ static cudaError_t tiny_num(const LaunchCtx& c, const Csr& A, const Csr& B, cons
   k<<<grid, 256, 0, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, nullptr, c_rp, c_ci, c_v, c.err);
   count_launch(c);
   return cudaGetLastError();
+}
+
+template <typename T, int E>
+static cudaError_t hash_num(const LaunchCtx& c, const Csr& A, const Csr& B, const T* av, const T* bv,
+                            const RowInfo& ri, int lo, int hi, const int32_t* c_rp, int32_t* c_ci, T* c_v,
+                            long long rows) {
+  auto k = k_hash_num<E, T>;
+  const int occ = kernel_blocks_per_sm(k, HASH_WARPS * 32, 0);
+  const int grid = persistent_grid(rows, HASH_WARPS, c.nsm, occ);
+  k<<<grid, HASH_WARPS * 32, 0, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, c_rp, c_ci, c_v, c.err);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+// Whether bins lo..hi hold no row (hist: rows per bin on the host, as the
+// symbolic pass read them; null: unknown, never empty).
+static bool empty_bins(const int* hist, int lo, int hi) {
+  if (!hist) return false;
+  for (int b = lo; b <= hi; ++b)
+    if (hist[b]) return false;
+  return true;
+}
+
+// Hash bins: 6 -> 1 product per lane (P <= 32), 7 -> 2 (P <= 64), 8 -> 4 (P <= 128).
+template <typename F1, typename F2, typename F4>
+static cudaError_t hash_dispatch(const int* hist, int lo, int hi, F1 f1, F2 f2, F4 f4) {
+  cudaError_t e = cudaSuccess;
+  auto clip = [&](int a, int b, auto f) -> cudaError_t {
+    const int l = lo > a ? lo : a, h = hi < b ? hi : b;
+    return (l <= h && !empty_bins(hist, l, h)) ? f(l, h) : cudaSuccess;
+  };
+  if ((e = clip(1, 6, f1))) return e;
+  if ((e = clip(7, 7, f2))) return e;
+  if ((e = clip(8, 8, f4))) return e;
+  return cudaSuccess;
 }
 
 template <typename T, int W>
@@ -92,12 +128,12 @@ static cudaError_t block_num(const LaunchCtx& c, const Csr& A, const Csr& B, con
 }
 
 template <typename F8, typename F16, typename F32, typename F64, typename F128, typename F256, typename F512>
-static cudaError_t tiny_dispatch(int lo, int hi, F8 f8, F16 f16, F32 f32, F64 f64, F128 f128, F256 f256,
-                                 F512 f512) {
+static cudaError_t tiny_dispatch(const int* hist, int lo, int hi, F8 f8, F16 f16, F32 f32, F64 f64, F128 f128,
+                                 F256 f256, F512 f512) {
   cudaError_t e = cudaSuccess;
   auto clip = [&](int a, int b, auto f) -> cudaError_t {
     const int l = lo > a ? lo : a, h = hi < b ? hi : b;
-    return l <= h ? f(l, h) : cudaSuccess;
+    return (l <= h && !empty_bins(hist, l, h)) ? f(l, h) : cudaSuccess;
   };
   if ((e = clip(1, 4, f8))) return e;
   if ((e = clip(5, 5, f16))) return e;
@@ -113,12 +149,12 @@ template <typename T>
 static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
                              const PathBins& pb, const Tuning& tu, const SplitInfo& sp, const T* av,
                              const T* bv, int32_t* cur, int32_t* nxt, const int32_t* c_rp, int32_t* c_ci,
-                             T* c_v, const int* path_rows, long long rows_wide) {
+                             T* c_v, const int* path_rows, long long rows_wide, const int* hist) {
   cudaError_t e = cudaSuccess;
   if (pb.hi[PATH_TINY] >= pb.lo[PATH_TINY]) {
     const long long rows = rows_in(path_rows, PATH_TINY);
     timer_mark(c, T_NUM_TINY, 0);
-    e = tiny_dispatch(pb.lo[PATH_TINY], pb.hi[PATH_TINY],
+    e = tiny_dispatch(hist, pb.lo[PATH_TINY], pb.hi[PATH_TINY],
         [&](int l, int h) { return tiny_num<T, 8, 1>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
         [&](int l, int h) { return tiny_num<T, 16, 1>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
         [&](int l, int h) { return tiny_num<T, 32, 1>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
@@ -127,6 +163,16 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
         [&](int l, int h) { return tiny_num<T, 32, 8>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
         [&](int l, int h) { return tiny_num<T, 32, 16>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); });
     timer_mark(c, T_NUM_TINY, 1);
+    if (e) return e;
+  }
+  if (pb.hi[PATH_HASH] >= pb.lo[PATH_HASH]) {
+    const long long rows = rows_in(path_rows, PATH_HASH);
+    timer_mark(c, T_NUM_HASH, 0);
+    e = hash_dispatch(hist, pb.lo[PATH_HASH], pb.hi[PATH_HASH],
+        [&](int l, int h) { return hash_num<T, 1>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
+        [&](int l, int h) { return hash_num<T, 2>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
+        [&](int l, int h) { return hash_num<T, 4>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); });
+    timer_mark(c, T_NUM_HASH, 1);
     if (e) return e;
   }
   // every other row: the warp-owned dense window up to tu.num_lo_block,
@@ -139,7 +185,7 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
       hi = pb.hi[p] > hi ? pb.hi[p] : hi;
     }
   const int blo = tu.num_lo_block > lo ? tu.num_lo_block : lo;
-  if (hi >= blo) {
+  if (hi >= blo && !empty_bins(hist, blo, hi)) {
     timer_mark(c, T_NUM_BLOCK, 0);
 #define SG_BLOCK_NUM(WW, NWW) e = block_num<T, WW, NWW>(c, A, B, av, bv, ri, blo, hi, sp, cur, nxt, c_rp, c_ci, c_v)
     // supported geometries (window columns, warps); others fall back to 8192 x 8
@@ -155,9 +201,9 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
 #undef SG_BLOCK_NUM
     timer_mark(c, T_NUM_BLOCK, 1);
     if (e) return e;
-    hi = blo - 1;
   }
-  if (hi >= lo) {
+  if (hi >= blo) hi = blo - 1;
+  if (hi >= lo && !empty_bins(hist, lo, hi)) {
     timer_mark(c, T_NUM_WARP, 0);
     switch (tu.window_warp) {
       case 2048: e = warp_num<T, 2048>(c, A, B, av, bv, ri, lo, hi, sp, cur, nxt, c_rp, c_ci, c_v, rows_wide); break;
@@ -173,12 +219,13 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
 cudaError_t launch_numeric(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri,
                            const PathBins& pb, const Tuning& tu, const SplitInfo& sp, int dtype,
                            const void* av, const void* bv, int32_t* cur, int32_t* nxt, const int32_t* c_rp,
-                           int32_t* c_ci, void* c_v, const int* path_rows, long long rows_wide) {
+                           int32_t* c_ci, void* c_v, const int* path_rows, long long rows_wide,
+                           const int* hist) {
   if (dtype == SPGEMM_F32)
     return numeric_t<float>(c, A, B, ri, pb, tu, sp, (const float*)av, (const float*)bv, cur, nxt, c_rp, c_ci,
-                            (float*)c_v, path_rows, rows_wide);
+                            (float*)c_v, path_rows, rows_wide, hist);
   return numeric_t<double>(c, A, B, ri, pb, tu, sp, (const double*)av, (const double*)bv, cur, nxt, c_rp, c_ci,
-                           (double*)c_v, path_rows, rows_wide);
+                           (double*)c_v, path_rows, rows_wide, hist);
 }
 
 }  // namespace sg

@@ -1,6 +1,7 @@
 // Symbolic pass: the number of distinct columns of every row of C
 // (Sec. 2.2: the union of the columns of the B rows a row of A touches).
 #include "launch_util.cuh"
+#include "rowhash.cuh"
 #include "rowpass.cuh"
 #include "symblock.cuh"
 
@@ -43,6 +44,31 @@ static cudaError_t tiny_dispatch(int lo, int hi, F8 f8, F16 f16, F32 f32, F64 f6
   if ((e = clip(8, 8, f128))) return e;
   if ((e = clip(9, 9, f256))) return e;
   if ((e = clip(10, 10, f512))) return e;
+  return cudaSuccess;
+}
+
+template <int E>
+static cudaError_t hash_sym(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri, int lo, int hi,
+                            int32_t* c_cnt, long long rows) {
+  auto k = k_hash_sym<E>;
+  const int occ = kernel_blocks_per_sm(k, HASH_WARPS * 32, 0);
+  const int grid = persistent_grid(rows, HASH_WARPS, c.nsm, occ);
+  k<<<grid, HASH_WARPS * 32, 0, c.stream>>>(A, B, ri, c.st, lo, hi, c_cnt, c.err);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+// Hash bins: 6 -> 1 product per lane (P <= 32), 7 -> 2 (P <= 64), 8 -> 4 (P <= 128).
+template <typename F1, typename F2, typename F4>
+static cudaError_t hash_dispatch(int lo, int hi, F1 f1, F2 f2, F4 f4) {
+  cudaError_t e = cudaSuccess;
+  auto clip = [&](int a, int b, auto f) -> cudaError_t {
+    const int l = lo > a ? lo : a, h = hi < b ? hi : b;
+    return l <= h ? f(l, h) : cudaSuccess;
+  };
+  if ((e = clip(1, 6, f1))) return e;
+  if ((e = clip(7, 7, f2))) return e;
+  if ((e = clip(8, 8, f4))) return e;
   return cudaSuccess;
 }
 
@@ -91,6 +117,16 @@ cudaError_t launch_symbolic(const LaunchCtx& c, const Csr& A, const Csr& B, cons
         [&](int l, int h) { return tiny_sym<32, 8>(c, A, B, ri, l, h, c_cnt, rows); },
         [&](int l, int h) { return tiny_sym<32, 16>(c, A, B, ri, l, h, c_cnt, rows); });
     timer_mark(c, T_SYM_TINY, 1);
+    if (e) return e;
+  }
+  if (pb.hi[PATH_HASH] >= pb.lo[PATH_HASH]) {
+    timer_mark(c, T_SYM_HASH, 0);
+    const long long rows = rows_in(path_rows, PATH_HASH);
+    e = hash_dispatch(pb.lo[PATH_HASH], pb.hi[PATH_HASH],
+        [&](int l, int h) { return hash_sym<1>(c, A, B, ri, l, h, c_cnt, rows); },
+        [&](int l, int h) { return hash_sym<2>(c, A, B, ri, l, h, c_cnt, rows); },
+        [&](int l, int h) { return hash_sym<4>(c, A, B, ri, l, h, c_cnt, rows); });
+    timer_mark(c, T_SYM_HASH, 1);
     if (e) return e;
   }
   if (pb.hi[PATH_WARP] >= pb.lo[PATH_WARP]) {

@@ -327,3 +327,95 @@ def test_block_window_fp32_exact(api, oracle_mod):
     R = oracle_mod.spgemm(A, B)
     assert_structure_equal(C, R)
     assert_values_exact(C.vals, R.vals)
+
+
+# ------------------------------------------------------------ hash path
+# Rows of 17..hash_max products go through the warp hash accumulator (one
+# shared-memory table per warp, cleared between the warp's rows); hash_max
+# -1 keeps the register sort, so each case also runs without the path.
+HASH_SETTINGS = [-1, 32, 64, 128]
+
+
+def _hash_rows(prod, hash_max):
+    hi = {-1: 0, 32: 32, 64: 64, 128: 128}[hash_max]
+    return int(((prod >= 17) & (prod <= hi)).sum())
+
+
+def _row_products(A, B):
+    blen = np.diff(B.row_ptr.astype(np.int64))
+    return np.add.reduceat(np.concatenate([blen[A.col_idx], [0]]),
+                           A.row_ptr[:-1].astype(np.int64)) * (np.diff(A.row_ptr) > 0)
+
+
+@pytest.mark.parametrize("hash_max", HASH_SETTINGS)
+@pytest.mark.parametrize("ncols", [300, 50000])
+def test_hash_path_mixed_rows(api, oracle_mod, hash_max, ncols):
+    """Rows of 0..~200 products: the register sort below 17, the hash bins
+    (1, 2 and 4 products per lane) and the window path above 128; a narrow
+    B (300 columns: many equal columns merge in each row) and a wide one."""
+    rng = np.random.default_rng(11 + ncols)
+    m, k = 4000, 900
+    A = gen.random_rows(m, k, rng.integers(0, 16, size=m), rng)
+    B = gen.random_rows(k, ncols, rng.integers(1, 17, size=k), rng)
+    C, stats = run(api, A, B, hash_max=hash_max)
+    R, S = oracle_with_scale(oracle_mod, A, B)
+    assert_structure_equal(C, R)
+    assert_values_close(C.vals, R.vals, S)
+    prod = _row_products(A, B)
+    assert stats[0] == int(prod.sum())
+    assert stats[2][1] == _hash_rows(prod, hash_max)
+    if hash_max == 128:
+        assert stats[2][1] > 1000
+
+
+@pytest.mark.parametrize("hash_max", HASH_SETTINGS)
+def test_hash_path_integer_bit_exact(api, oracle_mod, hash_max):
+    rng = np.random.default_rng(23)
+    A = gen.random_rows(2500, 700, rng.integers(0, 12, size=2500), rng, values="int")
+    B = gen.random_rows(700, 400, rng.integers(1, 14, size=700), rng, values="int")
+    C, _ = run(api, A, B, hash_max=hash_max)
+    R = oracle_mod.spgemm(A, B)
+    assert_structure_equal(C, R)
+    assert_values_exact(C.vals, R.vals)
+
+
+@pytest.mark.parametrize("hash_max", [-1, 128])
+def test_hash_path_fp32(api, oracle_mod, hash_max):
+    rng = np.random.default_rng(29)
+    A = gen.random_rows(3000, 800, rng.integers(0, 12, size=3000), rng)
+    B = gen.random_rows(800, 2000, rng.integers(1, 14, size=800), rng)
+    C, _ = run(api, A, B, dtype=torch.float32, hash_max=hash_max)
+    R, S = oracle_with_scale(oracle_mod, A, B)
+    assert_structure_equal(C, R)
+    assert_values_close(C.vals, R.vals, S, rtol=RTOL_F32)
+
+
+@pytest.mark.parametrize("hash_max", HASH_SETTINGS)
+def test_hash_path_3d_stencil_squared(api, oracle_mod, hash_max):
+    """3D 7-point operator on 20^3 squared: interior rows have 49 products
+    and 25 columns (bin 7), faces, edges and corners fewer; integer values,
+    so the result is bit-exact."""
+    A = gen.laplacian_3d(20)
+    C, stats = run(api, A, A, hash_max=hash_max)
+    R = oracle_mod.spgemm(A, A)
+    assert_structure_equal(C, R)
+    assert_values_exact(C.vals, R.vals)
+    assert stats[2][1] == _hash_rows(_row_products(A, A), hash_max)
+
+
+def test_hash_path_galerkin_small(api, oracle_mod):
+    """P^T (A P) on a 16^3 grid with 2x2x2 aggregation: both products have
+    rows in the hash bins (A P rows 7 products, P^T (AP) rows up to 8 times
+    A P's row sizes); exact integer sums."""
+    A = gen.laplacian_3d(16)
+    P = gen.aggregation_3d(16)
+    Pt = oracle_mod.transpose(P)
+    AP, _ = run(api, A, P)
+    R_AP = oracle_mod.spgemm(A, P)
+    assert_structure_equal(AP, R_AP)
+    assert_values_exact(AP.vals, R_AP.vals)
+    G, stats = run(api, Pt, R_AP)
+    R = oracle_mod.spgemm(Pt, R_AP)
+    assert_structure_equal(G, R)
+    assert_values_exact(G.vals, R.vals)
+    assert stats[2][1] > 0

@@ -179,3 +179,27 @@ def test_backward_full_size_65536(api, oracle_mod, dtype):
     assert max_rel_err(da.double().cpu().numpy(), rda, sa) <= tol
     assert max_rel_err(db.double().cpu().numpy(), rdb, sb) <= tol
     plan.close()
+
+
+def test_golden_worked_example_product_and_gradient(api):
+    """The hand-worked example of tests/golden (Sec. 2.2 row-wise
+    Gustavson): C and the gradient of the sum of C's entries through the
+    CUDA path, bit for bit (every value there is exact)."""
+    import os
+    from parity import load_golden
+    g = load_golden(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                 "gustavson_worked_example.txt"))
+    A, B = g["A"], g["B"]
+    dA, dB = api.DeviceCSR.from_host(A), api.DeviceCSR.from_host(B)
+    plan = api.Plan(dA, dB, backward=True)
+    rp, nnz = plan.symbolic()
+    ci, v = plan.numeric(dA.vals, dB.vals)
+    da, db = plan.backward(dA.vals, dB.vals, torch.ones(nnz, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    plan.check()
+    plan.close()
+    assert np.array_equal(rp.cpu().numpy().astype(np.int64), g["C"].row_ptr.astype(np.int64))
+    assert np.array_equal(ci.cpu().numpy(), g["C"].col_idx)
+    assert np.array_equal(v.cpu().numpy(), g["C"].vals)
+    assert np.array_equal(da.cpu().numpy(), g["dA"].vals)
+    assert np.array_equal(db.cpu().numpy(), g["dB"].vals)
