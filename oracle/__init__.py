@@ -13,7 +13,8 @@ rows; Table 1 for the per-nonzero product count).
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests
 (dense brute force, identity/permutation/diagonal products, stencil closed
 forms, the (A*B)*x = A*(B*x) invariant, finite differences for the
-gradient); none is "parity unpinned".
+gradient, a hand-worked example, triangle counts of graphs with known
+counts for the masked product); none is "parity unpinned".
 """
 from __future__ import annotations
 
@@ -65,6 +66,8 @@ def _load():
         lib.oracle_spmv.restype = None
         lib.oracle_row_products.argtypes = [I64, P, P, P, P]
         lib.oracle_row_products.restype = None
+        lib.oracle_masked.argtypes = [I64, I64, P, P, P, P, P, P, P, P, P, P]
+        lib.oracle_masked.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -155,6 +158,24 @@ def row_products(A: CSR, B: CSR) -> np.ndarray:
     arp, aci, brp = _c(A.row_ptr, np.int32), _c(A.col_idx, np.int32), _c(B.row_ptr, np.int32)
     out = np.empty(A.nrows, np.int64)
     lib.oracle_row_products(A.nrows, _p(arp), _p(aci), _p(brp), _p(out))
+    return out
+
+
+def masked(A: CSR, B: CSR, M: CSR, use_mask_values: bool = True) -> np.ndarray:
+    """C<M> = (A*B) .* M on M's pattern: for entry p = (i,j) of M,
+    M(i,j) * sum_k A(i,k) B(k,j) over the k with both entries stored (0 if
+    none), accumulated in the Gustavson product order of Sec. 2.2.  Without
+    ``use_mask_values`` M is a pure pattern (factor 1).  Returns nnz(M)
+    float64 values aligned with M's entries."""
+    lib = _load()
+    arp, aci, av = _c(A.row_ptr, np.int32), _c(A.col_idx, np.int32), _c(A.vals, np.float64)
+    brp, bci, bv = _c(B.row_ptr, np.int32), _c(B.col_idx, np.int32), _c(B.vals, np.float64)
+    mrp, mci = _c(M.row_ptr, np.int32), _c(M.col_idx, np.int32)
+    mv = _c(M.vals, np.float64) if use_mask_values else None
+    out = np.empty(M.nnz, np.float64)
+    if lib.oracle_masked(A.nrows, B.ncols, _p(arp), _p(aci), _p(av), _p(brp), _p(bci), _p(bv),
+                         _p(mrp), _p(mci), _p(mv) if mv is not None else None, _p(out)):
+        raise MemoryError("oracle allocation failed")
     return out
 
 

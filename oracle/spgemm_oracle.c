@@ -181,3 +181,44 @@ void oracle_row_products(int64_t m, const int32_t* a_rp, const int32_t* a_ci,
     prod[i] = s;
   }
 }
+
+/* Masked product C<M> = (A*B) .* M on M's pattern (the sampled product that
+ * triangle counting and Markov clustering use; Sec. 1 names both as SpGEMM
+ * applications).  c_v gets nnz(M) entries aligned with M's entries:
+ *   c_v[p] = m_v[p] * sum_k A(i,k) * B(k,j)   for entry p = (i,j) of M,
+ * the sum over the k with A(i,k) and B(k,j) both stored (0 when there is
+ * none: the output keeps all of M's pattern); without m_v (NULL) the factor
+ * is 1.  For each row: M's columns are scattered into a dense position array
+ * (pos[j] = p, -1 elsewhere), then the row's products are formed in A's
+ * stored order and, within each, B's stored order (the Gustavson order of
+ * Sec. 2.2), and each product whose column is in M's row is added to that
+ * entry's sum; the sums start at 0.0.  Returns 0, or -1 on allocation
+ * failure. */
+int oracle_masked(int64_t m, int64_t n,
+                  const int32_t* a_rp, const int32_t* a_ci, const double* a_v,
+                  const int32_t* b_rp, const int32_t* b_ci, const double* b_v,
+                  const int32_t* m_rp, const int32_t* m_ci, const double* m_v,
+                  double* c_v) {
+  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  if (!pos) return -1;
+  for (int64_t j = 0; j < n; ++j) pos[j] = -1;
+  for (int64_t i = 0; i < m; ++i) {
+    for (int32_t p = m_rp[i]; p < m_rp[i + 1]; ++p) {
+      pos[m_ci[p]] = p;
+      c_v[p] = 0.0;
+    }
+    for (int32_t e = a_rp[i]; e < a_rp[i + 1]; ++e) {
+      int32_t k = a_ci[e];
+      for (int32_t q = b_rp[k]; q < b_rp[k + 1]; ++q) {
+        int64_t p = pos[b_ci[q]];
+        if (p >= 0) c_v[p] = c_v[p] + a_v[e] * b_v[q];
+      }
+    }
+    for (int32_t p = m_rp[i]; p < m_rp[i + 1]; ++p) {
+      if (m_v) c_v[p] = c_v[p] * m_v[p];
+      pos[m_ci[p]] = -1;
+    }
+  }
+  free(pos);
+  return 0;
+}

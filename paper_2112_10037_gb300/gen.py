@@ -235,6 +235,22 @@ def permutation(perm) -> CSR:
     return _csr_from_sorted_coo(len(perm), len(perm), i, perm, np.ones(len(perm)))
 
 
+def lower_triangle_undirected(G: CSR) -> CSR:
+    """Strictly lower triangle L of the simple undirected graph on G's
+    pattern (G square; edges (i,j) and (j,i) are one edge, self-loops are
+    dropped), every stored value 1.0.  Triangle counting takes it as all three
+    operands of the masked product: sum((L*L) .* L) counts each triangle
+    i > k > j once."""
+    assert G.nrows == G.ncols
+    rows = np.repeat(np.arange(G.nrows, dtype=np.int64), np.diff(np.asarray(G.row_ptr, np.int64)))
+    cols = np.asarray(G.col_idx, np.int64)
+    hi, lo = np.maximum(rows, cols), np.minimum(rows, cols)
+    keep = hi != lo
+    key = np.unique(hi[keep] * G.ncols + lo[keep])
+    r, c = key // G.ncols, key % G.ncols
+    return _csr_from_sorted_coo(G.nrows, G.ncols, r, c, np.ones(len(key)))
+
+
 def from_dense(d: np.ndarray) -> CSR:
     """Pattern = nonzero entries of ``d`` (explicit zeros are not stored)."""
     d = np.asarray(d, np.float64)

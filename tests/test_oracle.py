@@ -330,3 +330,59 @@ def test_golden_worked_example(oracle_mod):
     da, db = oracle_mod.backward(A, B, C.row_ptr, C.col_idx, np.ones(C.nnz))
     assert np.array_equal(da, g["dA"].vals) and np.array_equal(g["dA"].col_idx, A.col_idx)
     assert np.array_equal(db, g["dB"].vals) and np.array_equal(g["dB"].col_idx, B.col_idx)
+
+
+# ------------------------------------------------------------ masked product
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_masked_brute_force(oracle_mod, seed):
+    """C<M> = (A*B) .* M against dense brute force on M's pattern (integer
+    values: exact), with and without M's values; rows and columns of M that
+    no product reaches included."""
+    A = gen.random_csr(37, 23, 0.2, seed, values="int", empty_rows=0.2)
+    B = gen.random_csr(23, 41, 0.2, seed + 10, values="int", empty_rows=0.2)
+    M = gen.random_csr(37, 41, 0.3, seed + 20, values="int")
+    P = _dense(A) @ _dense(B)
+    rows = np.repeat(np.arange(M.nrows), np.diff(np.asarray(M.row_ptr, np.int64)))
+    got = oracle_mod.masked(A, B, M)
+    assert np.array_equal(got, P[rows, M.col_idx] * M.vals)
+    got1 = oracle_mod.masked(A, B, M, use_mask_values=False)
+    assert np.array_equal(got1, P[rows, M.col_idx])
+
+
+def test_masked_real_values_and_full_mask(oracle_mod):
+    """Real values: within rounding of the dense product; with M = the
+    pattern of A*B the masked product is the product itself."""
+    A = gen.random_csr(50, 40, 0.15, 4)
+    B = gen.random_csr(40, 60, 0.15, 5)
+    C = oracle_mod.spgemm(A, B)
+    M = gen.CSR(C.nrows, C.ncols, C.row_ptr, C.col_idx, np.ones(C.nnz))
+    got = oracle_mod.masked(A, B, M)
+    rows = np.repeat(np.arange(M.nrows), np.diff(np.asarray(M.row_ptr, np.int64)))
+    dense = (_dense(A) @ _dense(B))[rows, M.col_idx]
+    scale = (np.abs(_dense(A)) @ np.abs(_dense(B)))[rows, M.col_idx]
+    assert np.all(np.abs(got - dense) <= 1e-14 * scale)
+    assert np.array_equal(got, C.vals)
+
+
+def _undirected(n, edges):
+    d = np.zeros((n, n))
+    for a, b in edges:
+        d[a, b] = d[b, a] = 1.0
+    return gen.lower_triangle_undirected(gen.from_dense(d))
+
+
+@pytest.mark.parametrize("name,n,edges,triangles", [
+    ("K12", 12, [(a, b) for a in range(12) for b in range(a)], 220),      # C(12,3)
+    ("K4 minus an edge", 4, [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3)], 2),
+    ("cycle C9", 9, [(a, (a + 1) % 9) for a in range(9)], 0),
+    ("wheel W10", 11, [(a, (a + 1) % 10) for a in range(10)] + [(10, a) for a in range(10)], 10),
+    ("3x4 grid", 12, [(r * 4 + c, r * 4 + c + 1) for r in range(3) for c in range(3)] +
+                     [(r * 4 + c, (r + 1) * 4 + c) for r in range(2) for c in range(4)], 0),
+])
+def test_masked_triangle_counts(oracle_mod, name, n, edges, triangles):
+    """Triangle counting (Sec. 1 lists it among SpGEMM's applications):
+    sum((L*L) .* L) over the strictly lower triangle L of the adjacency
+    matrix equals the graph's number of triangles (closed forms: C(n,3) for
+    K_n, n for the wheel with an n-cycle rim, none in a cycle or a grid)."""
+    L = _undirected(n, edges)
+    assert float(oracle_mod.masked(L, L, L).sum()) == triangles
