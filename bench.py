@@ -635,6 +635,95 @@ def run_backward(args):
     return out
 
 
+def run_triangles(args):
+    """Masked product (L*L) .* L on the strictly lower triangle L of the
+    undirected R-MAT graph (scale --rmat-scale, edge factor 16): the sum of
+    the output is the graph's triangle count.  GFLOP/s counts the products
+    of L*L that the row-wise pass forms (2 FLOP each); inputs resident, L2
+    flushed between steps; end to end adds the copy of L to the device and
+    of the output values back."""
+    import torch
+    from paper_2112_10037_gb300 import api, build as bld
+    bld.build()
+    dev = torch.device("cuda", 0)
+    L = gen.lower_triangle_undirected(gen.rmat(args.rmat_scale, 16))
+    prod = row_products(L, L)
+    products = int(prod.sum())
+    dL = api.DeviceCSR.from_host(L, device=dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device=dev)
+    out = None
+
+    def step():
+        nonlocal out
+        out = api.masked_spgemm(dL, dL, dL, use_mask_values=False)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    sampler.mark()
+    ts = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        t, _ = _events_ms(step, 1, stream)
+        ts.append(t)
+    clocks = sampler.stop()
+    ms = float(np.mean(ts))
+    triangles = int(round(float(out.sum().item())))
+    # byte model: L read as A (row pointers, columns, values), the rows of L
+    # touched as B (each once), L's pattern as the mask, the output written
+    arp = np.diff(L.row_ptr.astype(np.int64))
+    touched = np.unique(L.col_idx)
+    b_bytes = 8 * len(touched) + 12 * int(arp[touched].sum())
+    byte_model = (8 * L.nrows + 12 * L.nnz) + b_bytes + (8 * L.nrows + 4 * L.nnz) + 8 * L.nnz
+    peak, peak_kind = measured_hbm_peak()
+    achieved = byte_model / (ms / 1e3) / 1e9
+    # end to end: pinned host L -> device, masked product, values -> host
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_rp, h_ci, h_v = pin(L.row_ptr), pin(L.col_idx), pin(L.vals)
+    h_out = torch.empty(L.nnz, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        d = api.DeviceCSR(L.nrows, L.ncols, h_rp.to(dev, non_blocking=True), h_ci.to(dev, non_blocking=True),
+                          h_v.to(dev, non_blocking=True))
+        h_out.copy_(api.masked_spgemm(d, d, d, use_mask_values=False), non_blocking=True)
+
+    e2e_step()
+    t_e2e, e2e_ts = _events_ms(e2e_step, max(3, min(args.steps, 5)), stream)
+    desc = {"workload": "triangles_rmat_s%d_ef16_lower" % args.rmat_scale,
+            "matrix": "strictly lower triangle of the undirected R-MAT graph (scale %d, edge factor 16, "
+                      "(0.57,0.19,0.19,0.05), self-loops dropped, both directions merged), values 1" % args.rmat_scale,
+            "rows": L.nrows, "nnz_L": L.nnz, "products": products, "triangles": triangles,
+            "l2": "flushed between timed steps"}
+    res = _base_line("SpGEMM GFLOP/s (2*products/s), masked product (L*L).*L", 2.0 * products / (ms / 1e3) / 1e9,
+                     "GFLOP/s", args, ms, desc)
+    res["roofline"] = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                       "frac": round(achieved / peak, 4), "peak_kind": peak_kind + " hbm_gbs (copy)",
+                       "algorithmic_bytes": int(byte_model), "kernel": "k_masked", "traffic": None}
+    res["e2e"] = {"value": round(2.0 * products / (t_e2e / 1e3) / 1e9, 2), "unit": "GFLOP/s",
+                  "ms_per_step": round(t_e2e, 3), "ms_steps": [round(t, 3) for t in e2e_ts],
+                  "h2d_bytes_per_step": int(L.row_ptr.nbytes + L.col_idx.nbytes + L.vals.nbytes),
+                  "d2h_bytes_per_step": int(8 * L.nnz)}
+    res["gpu_launches"] = args.steps
+    res["clocks"] = clocks
+    if not args.no_cpu:
+        import oracle
+        oracle.build()
+        stride = max(1, int(round(products / 1e9)))   # about 10 s of single-threaded work
+        rows = np.arange(0, L.nrows, stride)
+        sub = oracle.select_rows(L, rows)
+        t0 = time.perf_counter()
+        oracle.masked(sub, L, sub, use_mask_values=False)
+        dt = time.perf_counter() - t0
+        p = int(prod[rows].sum())
+        res["cpu_baseline"] = {"value": 2.0 * p / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+                               "sample": "rows i = 0 mod %d of L (%d rows, %d products, %.1f s single-threaded)"
+                                         % (stride, len(rows), p, dt)}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -642,7 +731,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat",
-                    choices=["rmat", "lap2d", "stencil3d", "batched", "galerkin", "backward"])
+                    choices=["rmat", "lap2d", "stencil3d", "batched", "galerkin", "backward", "triangles"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-scale", type=float, default=0.1,
                     help="row-count scale of the batched instances (1.0 = rows in [1024, 200000])")
@@ -665,9 +754,10 @@ def main():
         A, B, desc = make_workload(args.workload, args.rmat_scale)
         print(json.dumps(run_reference(args, A, B, desc)), flush=True)
         return
-    if args.workload in ("batched", "galerkin", "backward"):
+    if args.workload in ("batched", "galerkin", "backward", "triangles"):
         if rank == 0:
-            runner = {"batched": run_batched, "galerkin": run_galerkin, "backward": run_backward}[args.workload]
+            runner = {"batched": run_batched, "galerkin": run_galerkin, "backward": run_backward,
+                      "triangles": run_triangles}[args.workload]
             print(json.dumps(runner(args)), flush=True)
         return
     if world > 1:

@@ -269,6 +269,26 @@ spgemm_status spgemm_transpose_noalloc(const spgemm_csr* M, int32_t dtype, int32
                                        int32_t* t_col_idx, void* t_vals, int32_t* t_src,
                                        spgemm_stream_t stream);
 
+/* Masked product C<M> = (A*B) .* M, the sampled SpGEMM of triangle counting
+ * and Markov clustering (two of the applications Sec. 1 lists), computed on
+ * the pattern of M with the row-wise Gustavson order of Sec. 2.2.  For entry
+ * p = (i,j) of M:
+ *   c_vals[p] = M(i,j) * sum_k A(i,k) * B(k,j),
+ * the sum over the k with A(i,k) and B(k,j) both stored; an entry of M that
+ * no product reaches gets 0 (the output keeps all of M's pattern).  With
+ * use_mask_values == 0 the factor M(i,j) is 1 and M.vals is not read.
+ *   A: m x k, B: k x n, M: m x n (device CSR; M's columns ascending in each
+ *   row, A's columns below k).  c_vals: nnz(M) values of `dtype`, aligned
+ *   with M's col_idx, caller-allocated, overwritten.
+ * Each product is rounded, then added to its entry's sum in shared memory;
+ * the order of the additions is not fixed, so real-valued sums may differ
+ * from a sequential sum in the last bits (integer-valued inputs are exact).
+ * Errors: SPGEMM_ERR_DIM_MISMATCH for inconsistent shapes,
+ * SPGEMM_ERR_INVALID_ARG for missing arrays or a bad dtype.  Does not
+ * block, allocates nothing, keeps no state. */
+spgemm_status spgemm_masked(const spgemm_csr* A, const spgemm_csr* B, const spgemm_csr* M, int32_t dtype,
+                            int32_t use_mask_values, void* c_vals, spgemm_stream_t stream);
+
 /* Frees the plan (host memory only).  NULL is allowed. */
 void spgemm_plan_destroy(spgemm_plan* plan);
 

@@ -81,6 +81,8 @@ _SIG = {
                          ctypes.c_int),
     "spgemm_transpose_check": ([_P, _P], ctypes.c_int),
     "spgemm_transpose_noalloc": ([ctypes.POINTER(spgemm_csr), ctypes.c_int32, _P, _P, _P, _P, _P], ctypes.c_int),
+    "spgemm_masked": ([ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
+                       ctypes.c_int32, ctypes.c_int32, _P, _P], ctypes.c_int),
     "spgemm_batch_workspace_size": ([ctypes.c_int32, ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
                                      ctypes.POINTER(spgemm_opts), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "spgemm_batched": ([ctypes.c_int32, ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
@@ -289,3 +291,9 @@ def spgemm_transpose_noalloc(M: spgemm_csr, dtype: int, t_row_ptr: int, t_col_id
                              stream: int) -> None:
     _check(lib().spgemm_transpose_noalloc(ctypes.byref(M), dtype, _P(t_row_ptr), _P(t_col_idx), _P(t_vals),
                                           _P(t_src), _P(stream)), "spgemm_transpose_noalloc")
+
+
+def spgemm_masked(A: spgemm_csr, B: spgemm_csr, M: spgemm_csr, dtype: int, use_mask_values: bool, c_vals: int,
+                  stream: int) -> None:
+    _check(lib().spgemm_masked(ctypes.byref(A), ctypes.byref(B), ctypes.byref(M), dtype,
+                               1 if use_mask_values else 0, _P(c_vals), _P(stream)), "spgemm_masked")

@@ -329,6 +329,21 @@ def transpose(M: DeviceCSR, want_src: bool = False, dtype=None, stream=None):
     return (T, src) if want_src else T
 
 
+def masked_spgemm(A: DeviceCSR, B: DeviceCSR, M: DeviceCSR, use_mask_values: bool = True, dtype=None,
+                  stream=None) -> torch.Tensor:
+    """C<M> = (A*B) .* M on M's pattern (``spgemm_masked``): a tensor of
+    nnz(M) values aligned with M's col_idx, entry (i,j) holding
+    M(i,j) * sum_k A(i,k) B(k,j) (0 where no product reaches it); without
+    ``use_mask_values`` M is a pure pattern.  Asynchronous on ``stream``."""
+    dtype = dtype or A.vals.dtype
+    out = torch.empty(M.nnz, dtype=dtype, device=M.row_ptr.device)
+    if use_mask_values and M.vals is not None and M.vals.dtype != dtype:
+        raise TypeError("mask values must have the product's dtype")
+    nat.spgemm_masked(A.c_struct(), B.c_struct(), M.c_struct(), _DT[dtype], bool(use_mask_values),
+                      out.data_ptr() if M.nnz else 0, _stream_handle(stream))
+    return out
+
+
 def _plan_backward(self, a_vals, b_vals, dc_vals, need_a=True, need_b=True):
     """(dA, dB) for dC on this plan's C pattern (``spgemm_backward``)."""
     dev = self.workspace.device
