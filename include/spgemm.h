@@ -280,9 +280,11 @@ spgemm_status spgemm_transpose_noalloc(const spgemm_csr* M, int32_t dtype, int32
  *   A: m x k, B: k x n, M: m x n (device CSR; M's columns ascending in each
  *   row, A's columns below k).  c_vals: nnz(M) values of `dtype`, aligned
  *   with M's col_idx, caller-allocated, overwritten.
- * Each product is rounded, then added to its entry's sum in shared memory;
- * the order of the additions is not fixed, so real-valued sums may differ
- * from a sequential sum in the last bits (integer-valued inputs are exact).
+ * c_vals is zeroed by the call, then each product is rounded and added to
+ * its entry's sum (shared-memory and global FP64 reductions), and the
+ * finished sums are multiplied by M's values.  The order of the additions
+ * is not fixed, so real-valued sums may differ from a sequential sum in the
+ * last bits (integer-valued inputs are exact).
  * Errors: SPGEMM_ERR_DIM_MISMATCH for inconsistent shapes,
  * SPGEMM_ERR_INVALID_ARG for missing arrays or a bad dtype.  Does not
  * block, allocates nothing, keeps no state. */

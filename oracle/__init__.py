@@ -179,6 +179,23 @@ def masked(A: CSR, B: CSR, M: CSR, use_mask_values: bool = True) -> np.ndarray:
     return out
 
 
+def omar(A: CSR, pes: int) -> float:
+    """Off-chip memory access reduction (Eq. 1) of the buffering scheme of
+    Sec. 3: rows are taken pes at a time (one per computing unit), and one
+    CSV vector is the group's nonzeros in one column, so all of them share
+    one read of that row of B.  OMAR(%) = sum over the nonzero vectors v of
+    (nnz(v) - 1), divided by nnz(A), times 100.  Counted vector by vector:
+    for each group of rows, the nonzeros per column (np.unique with counts)."""
+    rp = np.asarray(A.row_ptr, np.int64)
+    total = 0
+    for g0 in range(0, A.nrows, pes):
+        cols = np.asarray(A.col_idx[rp[g0]:rp[min(g0 + pes, A.nrows)]])
+        if len(cols):
+            _, counts = np.unique(cols, return_counts=True)
+            total += int((counts - 1).sum())
+    return 100.0 * total / A.nnz if A.nnz else 0.0
+
+
 def select_rows(A: CSR, rows) -> CSR:
     """The sub-matrix of the given rows of A (input slicing, no arithmetic)."""
     rows = np.asarray(rows, np.int64)

@@ -185,6 +185,39 @@ def spgemm(A: DeviceCSR, B: DeviceCSR, dtype=None, **opt_kw) -> DeviceCSR:
     return DeviceCSR(plan.nrows, B.ncols, rp, ci, v)
 
 
+def spgemm_colwise(A: DeviceCSR, B: DeviceCSR, dtype=None, **opt_kw) -> DeviceCSR:
+    """C = A*B by the column-wise Gustavson method (Sec. 2.2: the row-wise
+    method with rows and columns switched, column j of C the sum of the
+    columns A(:,k) scaled by B(k,j)): C^T = B^T A^T computed row by row on
+    the transposes, then transposed back.  Same C as ``spgemm``; the sums
+    run in B's column order instead of A's row order."""
+    dtype = dtype or (A.vals.dtype if A.vals is not None else torch.float64)
+    Ct = spgemm(transpose(B, dtype=dtype), transpose(A, dtype=dtype), dtype=dtype, **opt_kw)
+    return transpose(Ct, dtype=dtype)
+
+
+def omar(A: DeviceCSR, pes: int, stream=None) -> float:
+    """Off-chip memory access reduction (Eq. 1) of the buffering scheme of
+    Sec. 3 for ``pes`` computing units: rows are taken ``pes`` at a time and
+    the group's nonzeros in one column (one CSV vector) share one read of
+    that row of B.  The number of such vectors is nnz(G*A) for the 0/1
+    matrix G that sums each group of rows, so the symbolic pass of this
+    library counts them; OMAR(%) = 100 * (nnz(A) - nnz(G*A)) / nnz(A)."""
+    if pes < 1:
+        raise ValueError("pes must be at least 1")
+    if A.nnz == 0:
+        return 0.0
+    dev = A.row_ptr.device
+    groups = (A.nrows + pes - 1) // pes
+    g_rp = torch.clamp(torch.arange(groups + 1, device=dev, dtype=torch.int64) * pes, max=A.nrows).to(torch.int32)
+    g_ci = torch.arange(A.nrows, device=dev, dtype=torch.int32)
+    G = DeviceCSR(groups, A.nrows, g_rp, g_ci, None)
+    plan = Plan(G, A, stream=stream)
+    _, vectors = plan.symbolic()
+    plan.close()
+    return 100.0 * (A.nnz - vectors) / A.nnz
+
+
 _streams = {}
 _staging = {}
 _staging_lock = threading.Lock()

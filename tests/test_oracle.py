@@ -386,3 +386,28 @@ def test_masked_triangle_counts(oracle_mod, name, n, edges, triangles):
     K_n, n for the wheel with an n-cycle rim, none in a cycle or a grid)."""
     L = _undirected(n, edges)
     assert float(oracle_mod.masked(L, L, L).sum()) == triangles
+
+
+# ------------------------------------------------------------------- OMAR
+def test_omar_hand_example(oracle_mod):
+    """Eq. 1 by hand: rows {0,1}, {1,2}, {0,3}, {3} with two computing
+    units: vectors (group 0: column 0 x1, column 1 x2, column 2 x1;
+    group 1: column 0 x1, column 3 x2) give (2-1) + (2-1) = 2 shared reads
+    out of 7 nonzeros."""
+    d = np.zeros((4, 4))
+    for r, cs in enumerate([(0, 1), (1, 2), (0, 3), (3,)]):
+        d[r, list(cs)] = 1.0
+    A = gen.from_dense(d)
+    assert abs(oracle_mod.omar(A, 2) - 100.0 * 2 / 7) < 1e-12
+    assert oracle_mod.omar(A, 1) == 0.0
+    assert abs(oracle_mod.omar(A, 4) - 100.0 * 3 / 7) < 1e-12   # columns 0,1,3 read twice each
+
+
+@pytest.mark.parametrize("m,n,pes", [(10, 7, 3), (12, 5, 4), (9, 1, 32), (1, 6, 8)])
+def test_omar_closed_forms(oracle_mod, m, n, pes):
+    """Dense rows (every group shares all n columns): 1 - ceil(m/P)/m;
+    a diagonal: no sharing at all."""
+    A = gen.from_dense(np.ones((m, n)))
+    groups = -(-m // pes)
+    assert abs(oracle_mod.omar(A, pes) - 100.0 * (1 - groups / m)) < 1e-12
+    assert oracle_mod.omar(gen.identity(m), pes) == 0.0
