@@ -724,6 +724,42 @@ def run_triangles(args):
     return res
 
 
+def run_omar(args):
+    """OMAR (Eq. 1) of the buffering scheme of Sec. 3 for 2..32 computing
+    units on the R-MAT and 3D stencil matrices, computed on the device (one
+    symbolic pass of the grouping matrix times A per P); the oracle's count
+    beside it for P = 32 (host, single thread)."""
+    import torch
+    from paper_2112_10037_gb300 import api, build as bld
+    bld.build()
+    stream = torch.cuda.current_stream()
+    pes = [2, 4, 8, 16, 32]
+    res = {}
+    for name, M in (("rmat_s%d_ef16" % args.rmat_scale, gen.rmat(args.rmat_scale, 16)),
+                    ("laplacian3d_96", gen.laplacian_3d(96))):
+        dM = api.DeviceCSR.from_host(M)
+        vals = {}
+        for p in pes:
+            for _ in range(args.warmup):
+                api.omar(dM, p)
+            box = {}
+            ms, _ = _events_ms(lambda: box.update(v=api.omar(dM, p)), args.steps, stream)
+            vals[p] = {"omar_pct": round(box["v"], 4), "ms": round(ms, 4)}
+        entry = {"nnz": M.nnz, "by_pes": vals}
+        if not args.no_cpu:
+            import oracle
+            t0 = time.perf_counter()
+            ref = oracle.omar(M, 32)
+            entry["oracle_32"] = {"omar_pct": round(ref, 4), "s": round(time.perf_counter() - t0, 3),
+                                  "equal": ref == vals[32]["omar_pct"] or abs(ref - vals[32]["omar_pct"]) < 1e-4}
+        res[name] = entry
+    first = next(iter(res))
+    out = _base_line("OMAR (%) of Eq. 1 at 32 computing units", res[first]["by_pes"][32]["omar_pct"], "%", args,
+                     res[first]["by_pes"][32]["ms"], {"workload": "omar_rmat_s%d_and_laplacian3d_96" % args.rmat_scale})
+    out["matrices"] = res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -731,7 +767,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat",
-                    choices=["rmat", "lap2d", "stencil3d", "batched", "galerkin", "backward", "triangles"])
+                    choices=["rmat", "lap2d", "stencil3d", "batched", "galerkin", "backward", "triangles", "omar"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-scale", type=float, default=0.1,
                     help="row-count scale of the batched instances (1.0 = rows in [1024, 200000])")
@@ -754,10 +790,10 @@ def main():
         A, B, desc = make_workload(args.workload, args.rmat_scale)
         print(json.dumps(run_reference(args, A, B, desc)), flush=True)
         return
-    if args.workload in ("batched", "galerkin", "backward", "triangles"):
+    if args.workload in ("batched", "galerkin", "backward", "triangles", "omar"):
         if rank == 0:
             runner = {"batched": run_batched, "galerkin": run_galerkin, "backward": run_backward,
-                      "triangles": run_triangles}[args.workload]
+                      "triangles": run_triangles, "omar": run_omar}[args.workload]
             print(json.dumps(runner(args)), flush=True)
         return
     if world > 1:
