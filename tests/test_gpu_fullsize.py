@@ -100,3 +100,25 @@ def test_fullsize_structure(full):
         assert bool(ok.all()), "columns not ascending inside a row near entry %d" % off
     assert int(ci.min()) >= 0 and int(ci.max()) < A.ncols
     assert bool(torch.isfinite(v).all())
+
+
+def test_fullsize_triangle_counting_exact(api, oracle_mod):
+    """The triangle-counting workload of bench.py at full size (masked
+    product (L*L) .* L on the undirected R-MAT scale-18 graph's lower
+    triangle): every one of the nnz(L) outputs exact against the oracle
+    (integer sums), and the same triangle count."""
+    L = gen.lower_triangle_undirected(gen.rmat(18, 16))
+    dL = api.DeviceCSR.from_host(L)
+    got = api.masked_spgemm(dL, dL, dL, use_mask_values=False).cpu().numpy()
+    ref = oracle_mod.masked(L, L, L, use_mask_values=False)
+    assert np.array_equal(got, ref)
+    assert int(ref.sum()) > 0
+
+
+def test_fullsize_omar(full, api, oracle_mod):
+    """OMAR (Eq. 1) of the benchmark matrix at 2..32 computing units against
+    the oracle's vector-by-vector count."""
+    A = full[0]
+    dA = api.DeviceCSR.from_host(A)
+    for pes in (2, 4, 8, 16, 32):
+        assert api.omar(dA, pes) == oracle_mod.omar(A, pes)
