@@ -68,6 +68,8 @@ def _load():
         lib.oracle_row_products.restype = None
         lib.oracle_masked.argtypes = [I64, I64, P, P, P, P, P, P, P, P, P, P]
         lib.oracle_masked.restype = ctypes.c_int
+        lib.oracle_masked_semiring.argtypes = [I64, I64, ctypes.c_int32, P, P, P, P, P, P, P, P, P]
+        lib.oracle_masked_semiring.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -176,6 +178,27 @@ def masked(A: CSR, B: CSR, M: CSR, use_mask_values: bool = True) -> np.ndarray:
     if lib.oracle_masked(A.nrows, B.ncols, _p(arp), _p(aci), _p(av), _p(brp), _p(bci), _p(bv),
                          _p(mrp), _p(mci), _p(mv) if mv is not None else None, _p(out)):
         raise MemoryError("oracle allocation failed")
+    return out
+
+
+SEMIRINGS = {"plus_times": 0, "min_plus": 1, "max_plus": 2, "or_and": 3}
+
+
+def masked_semiring(A: CSR, B: CSR, M: CSR, semiring: str) -> np.ndarray:
+    """Masked product over a semiring on M's pattern (M's values unused):
+    min-plus (min of a + b, +inf where no product reaches), max-plus (max of
+    a + b, -inf), or-and (1.0 where some product has both factors nonzero,
+    else 0.0), plus-times (the sum of a * b).  The products run in the
+    row-wise Gustavson order of Sec. 2.2."""
+    lib = _load()
+    arp, aci, av = _c(A.row_ptr, np.int32), _c(A.col_idx, np.int32), _c(A.vals, np.float64)
+    brp, bci, bv = _c(B.row_ptr, np.int32), _c(B.col_idx, np.int32), _c(B.vals, np.float64)
+    mrp, mci = _c(M.row_ptr, np.int32), _c(M.col_idx, np.int32)
+    out = np.empty(M.nnz, np.float64)
+    r = lib.oracle_masked_semiring(A.nrows, B.ncols, SEMIRINGS[semiring], _p(arp), _p(aci), _p(av), _p(brp),
+                                   _p(bci), _p(bv), _p(mrp), _p(mci), _p(out))
+    if r:
+        raise MemoryError("oracle allocation failed") if r == -1 else ValueError(semiring)
     return out
 
 

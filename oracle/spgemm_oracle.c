@@ -222,3 +222,51 @@ int oracle_masked(int64_t m, int64_t n,
   free(pos);
   return 0;
 }
+
+/* Semiring versions of the masked product (the same row-wise Gustavson
+ * order, products kept where M's row has their column; M's values are not
+ * read).  For entry p = (i,j) of M, c_v[p] = the "sum" over the k with A(i,k)
+ * and B(k,j) both stored of the "product" of A(i,k) and B(k,j), starting
+ * from the semiring's zero (what an entry no product reaches keeps):
+ *   semiring 1, min-plus: sum = min, product = a + b, zero = +infinity;
+ *   semiring 2, max-plus: sum = max, product = a + b, zero = -infinity;
+ *   semiring 3, or-and:   sum = or, product = (a != 0 and b != 0), values
+ *                         1.0 (true) and 0.0 (false), zero = 0.0;
+ * semiring 0 is the ordinary (plus, times) masked product of oracle_masked
+ * without M's values.  Sec. 1 lists all-pairs shortest paths (min-plus)
+ * among SpGEMM's applications.  Returns 0, -1 on allocation failure, -2 for
+ * an unknown semiring. */
+int oracle_masked_semiring(int64_t m, int64_t n, int32_t semiring,
+                           const int32_t* a_rp, const int32_t* a_ci, const double* a_v,
+                           const int32_t* b_rp, const int32_t* b_ci, const double* b_v,
+                           const int32_t* m_rp, const int32_t* m_ci, double* c_v) {
+  if (semiring < 0 || semiring > 3) return -2;
+  const double inf = 1.0 / 0.0;
+  const double zero = semiring == 1 ? inf : (semiring == 2 ? -inf : 0.0);
+  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  if (!pos) return -1;
+  for (int64_t j = 0; j < n; ++j) pos[j] = -1;
+  for (int64_t i = 0; i < m; ++i) {
+    for (int32_t p = m_rp[i]; p < m_rp[i + 1]; ++p) {
+      pos[m_ci[p]] = p;
+      c_v[p] = zero;
+    }
+    for (int32_t e = a_rp[i]; e < a_rp[i + 1]; ++e) {
+      int32_t k = a_ci[e];
+      for (int32_t q = b_rp[k]; q < b_rp[k + 1]; ++q) {
+        int64_t p = pos[b_ci[q]];
+        if (p < 0) continue;
+        double a = a_v[e], b = b_v[q];
+        switch (semiring) {
+          case 0: c_v[p] = c_v[p] + a * b; break;
+          case 1: if (a + b < c_v[p]) c_v[p] = a + b; break;
+          case 2: if (a + b > c_v[p]) c_v[p] = a + b; break;
+          default: if (a != 0.0 && b != 0.0) c_v[p] = 1.0; break;
+        }
+      }
+    }
+    for (int32_t p = m_rp[i]; p < m_rp[i + 1]; ++p) pos[m_ci[p]] = -1;
+  }
+  free(pos);
+  return 0;
+}

@@ -411,3 +411,118 @@ def test_omar_closed_forms(oracle_mod, m, n, pes):
     groups = -(-m // pes)
     assert abs(oracle_mod.omar(A, pes) - 100.0 * (1 - groups / m)) < 1e-12
     assert oracle_mod.omar(gen.identity(m), pes) == 0.0
+
+
+# ------------------------------------------------------------ semirings
+def _semiring_brute(A, B, M, semiring):
+    """Entry by entry from the definition, on dense arrays: for (i,j) in M,
+    reduce over the k where A(i,k) and B(k,j) are both stored."""
+    Ad, Bd = _dense(A), _dense(B)
+    Ap, Bp = _pattern(A), _pattern(B)
+    rows = np.repeat(np.arange(M.nrows), np.diff(np.asarray(M.row_ptr, np.int64)))
+    out = []
+    for i, j in zip(rows, M.col_idx):
+        ks = np.flatnonzero(Ap[i] & Bp[:, j])
+        a, b = Ad[i, ks], Bd[ks, j]
+        if semiring == "min_plus":
+            out.append((a + b).min() if len(ks) else np.inf)
+        elif semiring == "max_plus":
+            out.append((a + b).max() if len(ks) else -np.inf)
+        else:
+            out.append(1.0 if np.any((a != 0) & (b != 0)) else 0.0)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("semiring", ["min_plus", "max_plus", "or_and"])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_semiring_brute_force(oracle_mod, semiring, seed):
+    """Integer values in [-3, 3] (stored zeros included, which or-and must
+    treat as false), empty rows, mask entries no product reaches."""
+    A = gen.random_csr(23, 17, 0.25, seed, values="int", empty_rows=0.2)
+    B = gen.random_csr(17, 29, 0.25, seed + 5, values="int", empty_rows=0.2)
+    M = gen.random_csr(23, 29, 0.4, seed + 9)
+    assert np.array_equal(oracle_mod.masked_semiring(A, B, M, semiring), _semiring_brute(A, B, M, semiring))
+
+
+def _with_zero_diagonal(d):
+    """CSR of the positive weights in d (zero diagonal) plus a stored 0.0 on
+    every diagonal entry (a path may stay put at no cost)."""
+    n = d.shape[0]
+    P = gen.from_dense(d + np.eye(n))
+    rows = np.repeat(np.arange(n), np.diff(np.asarray(P.row_ptr, np.int64)))
+    return gen.CSR(n, n, P.row_ptr, P.col_idx, np.where(rows == P.col_idx, 0.0, d[rows, P.col_idx]))
+
+
+def _square_to_fixpoint(oracle_mod, D, semiring):
+    """D <- D (x) D over the pattern of D*D until nothing changes (the
+    pattern of D*D contains D's because D's diagonal is stored)."""
+    for _ in range(20):
+        P = oracle_mod.spgemm(D, D)
+        vals = oracle_mod.masked_semiring(D, D, P, semiring)
+        Dn = gen.CSR(P.nrows, P.ncols, P.row_ptr, P.col_idx, vals)
+        if Dn.nnz == D.nnz and np.array_equal(Dn.col_idx, D.col_idx) and np.array_equal(Dn.vals, D.vals):
+            return Dn
+        D = Dn
+    raise AssertionError("no fixpoint")
+
+
+def test_min_plus_all_pairs_shortest_paths(oracle_mod):
+    """Repeated min-plus squaring of the weighted adjacency (zero diagonal)
+    reaches the all-pairs shortest-path distances: checked against scipy's
+    Dijkstra; pairs outside the final pattern are unreachable there."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import shortest_path
+    rng = np.random.default_rng(4)
+    n = 60
+    d = np.zeros((n, n))
+    for _ in range(150):
+        a, b = rng.integers(0, n, 2)
+        if a != b:
+            d[a, b] = float(rng.integers(1, 20))
+    D = _square_to_fixpoint(oracle_mod, _with_zero_diagonal(d), "min_plus")
+    ref = shortest_path(csr_matrix(d), method="D", directed=True)
+    got = np.full((n, n), np.inf)
+    rows = np.repeat(np.arange(n), np.diff(np.asarray(D.row_ptr, np.int64)))
+    got[rows, D.col_idx] = D.vals
+    assert np.array_equal(got, ref)
+
+
+def test_max_plus_longest_paths_in_a_dag(oracle_mod):
+    """Repeated max-plus squaring of a DAG's weighted adjacency (zero
+    diagonal) gives the longest path between every connected pair: checked
+    against dynamic programming over the topological order."""
+    rng = np.random.default_rng(7)
+    n = 40
+    d = np.zeros((n, n))
+    edges = []
+    for _ in range(90):
+        a, b = sorted(rng.integers(0, n, 2))
+        if a != b:
+            d[a, b] = float(rng.integers(1, 9))
+            edges.append((a, b))
+    D = _square_to_fixpoint(oracle_mod, _with_zero_diagonal(d), "max_plus")
+    best = np.full((n, n), -np.inf)
+    for s in range(n):
+        best[s, s] = 0.0
+        for u in range(s, n):          # vertices in topological (index) order
+            if best[s, u] == -np.inf:
+                continue
+            for v in np.flatnonzero(d[u]):
+                best[s, v] = max(best[s, v], best[s, u] + d[u, v])
+    got = np.full((n, n), -np.inf)
+    rows = np.repeat(np.arange(n), np.diff(np.asarray(D.row_ptr, np.int64)))
+    got[rows, D.col_idx] = D.vals
+    assert np.array_equal(got, best)
+
+
+def test_or_and_is_the_boolean_product(oracle_mod):
+    """Or-and over the full product pattern: 1 exactly where some product
+    has both factors nonzero, i.e. the Boolean matrix product of the
+    nonzero patterns."""
+    A = gen.random_csr(30, 20, 0.2, 3, values="int")
+    B = gen.random_csr(20, 25, 0.2, 4, values="int")
+    C = oracle_mod.spgemm(A, B)
+    got = oracle_mod.masked_semiring(A, B, C, "or_and")
+    boolean = ((_dense(A) != 0).astype(int) @ (_dense(B) != 0).astype(int)) > 0
+    rows = np.repeat(np.arange(C.nrows), np.diff(np.asarray(C.row_ptr, np.int64)))
+    assert np.array_equal(got, boolean[rows, C.col_idx].astype(float))
