@@ -291,6 +291,31 @@ spgemm_status spgemm_transpose_noalloc(const spgemm_csr* M, int32_t dtype, int32
 spgemm_status spgemm_masked(const spgemm_csr* A, const spgemm_csr* B, const spgemm_csr* M, int32_t dtype,
                             int32_t use_mask_values, void* c_vals, spgemm_stream_t stream);
 
+/* Semirings of spgemm_semiring: the "sum" that merges the products of one
+ * entry, the "product" of A(i,k) and B(k,j), and the zero an entry keeps when
+ * no product reaches it. */
+typedef enum spgemm_semiring_kind {
+  SPGEMM_PLUS_TIMES = 0, /* sum +,   product a*b,                       zero 0     */
+  SPGEMM_MIN_PLUS = 1,   /* sum min, product a+b,                       zero +inf  */
+  SPGEMM_MAX_PLUS = 2,   /* sum max, product a+b,                       zero -inf  */
+  SPGEMM_OR_AND = 3      /* sum or,  product (a != 0 and b != 0) as 1/0, zero 0     */
+} spgemm_semiring_kind;
+
+/* The masked product of spgemm_masked over another semiring (all-pairs
+ * shortest paths by repeated min-plus squaring, longest paths, reachability;
+ * Sec. 1 lists shortest paths among SpGEMM's applications), on the pattern
+ * of M with the row-wise Gustavson order of Sec. 2.2:
+ *   c_vals[p] = sum over k of product(A(i,k), B(k,j))  for entry p = (i,j) of M,
+ * over the k with A(i,k) and B(k,j) both stored, and the semiring's zero where
+ * there is none.  M's values are not read.  With M the pattern of A*B (from
+ * spgemm_symbolic and spgemm_numeric) this is the full semiring product.
+ * Min-plus, max-plus and or-and results do not depend on the order of the
+ * sums, so they are exact; plus-times is spgemm_masked without M's values.
+ * Shapes, arrays and errors as spgemm_masked; SPGEMM_ERR_INVALID_ARG for an
+ * unknown semiring.  Does not block, allocates nothing, keeps no state. */
+spgemm_status spgemm_semiring(const spgemm_csr* A, const spgemm_csr* B, const spgemm_csr* M, int32_t dtype,
+                              int32_t semiring, void* c_vals, spgemm_stream_t stream);
+
 /* Frees the plan (host memory only).  NULL is allowed. */
 void spgemm_plan_destroy(spgemm_plan* plan);
 

@@ -83,6 +83,8 @@ _SIG = {
     "spgemm_transpose_noalloc": ([ctypes.POINTER(spgemm_csr), ctypes.c_int32, _P, _P, _P, _P, _P], ctypes.c_int),
     "spgemm_masked": ([ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
                        ctypes.c_int32, ctypes.c_int32, _P, _P], ctypes.c_int),
+    "spgemm_semiring": ([ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
+                         ctypes.c_int32, ctypes.c_int32, _P, _P], ctypes.c_int),
     "spgemm_batch_workspace_size": ([ctypes.c_int32, ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
                                      ctypes.POINTER(spgemm_opts), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
     "spgemm_batched": ([ctypes.c_int32, ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
@@ -297,3 +299,12 @@ def spgemm_masked(A: spgemm_csr, B: spgemm_csr, M: spgemm_csr, dtype: int, use_m
                   stream: int) -> None:
     _check(lib().spgemm_masked(ctypes.byref(A), ctypes.byref(B), ctypes.byref(M), dtype,
                                1 if use_mask_values else 0, _P(c_vals), _P(stream)), "spgemm_masked")
+
+
+SPGEMM_PLUS_TIMES, SPGEMM_MIN_PLUS, SPGEMM_MAX_PLUS, SPGEMM_OR_AND = 0, 1, 2, 3
+
+
+def spgemm_semiring(A: spgemm_csr, B: spgemm_csr, M: spgemm_csr, dtype: int, semiring: int, c_vals: int,
+                    stream: int) -> None:
+    _check(lib().spgemm_semiring(ctypes.byref(A), ctypes.byref(B), ctypes.byref(M), dtype, semiring, _P(c_vals),
+                                 _P(stream)), "spgemm_semiring")

@@ -377,6 +377,38 @@ def masked_spgemm(A: DeviceCSR, B: DeviceCSR, M: DeviceCSR, use_mask_values: boo
     return out
 
 
+SEMIRINGS = {"plus_times": nat.SPGEMM_PLUS_TIMES, "min_plus": nat.SPGEMM_MIN_PLUS, "max_plus": nat.SPGEMM_MAX_PLUS,
+             "or_and": nat.SPGEMM_OR_AND}
+
+
+def masked_semiring(A: DeviceCSR, B: DeviceCSR, M: DeviceCSR, semiring: str = "min_plus", dtype=None,
+                    stream=None) -> torch.Tensor:
+    """The masked product over a semiring on M's pattern
+    (``spgemm_semiring``): nnz(M) values aligned with M's col_idx, entry
+    (i,j) the semiring sum over k of product(A(i,k), B(k,j)) -- min of a + b
+    ("min_plus", +inf where no product reaches), max of a + b ("max_plus",
+    -inf), 1/0 for some product with both factors nonzero ("or_and"), or the
+    ordinary sum of a * b ("plus_times").  M's values are not read."""
+    dtype = dtype or A.vals.dtype
+    out = torch.empty(M.nnz, dtype=dtype, device=M.row_ptr.device)
+    nat.spgemm_semiring(A.c_struct(), B.c_struct(), M.c_struct(), _DT[dtype], SEMIRINGS[semiring],
+                        out.data_ptr() if M.nnz else 0, _stream_handle(stream))
+    return out
+
+
+def spgemm_semiring(A: DeviceCSR, B: DeviceCSR, semiring: str = "min_plus", dtype=None, **opt_kw) -> DeviceCSR:
+    """C = A (x) B over a semiring on the full pattern of A*B (the product's
+    structure from the symbolic and numeric passes, then the semiring values
+    on it)."""
+    dtype = dtype or A.vals.dtype
+    plan = Plan(A, B, dtype=dtype, **opt_kw)
+    rp, _ = plan.symbolic()
+    ci, _ = plan.numeric(A.vals, B.vals)
+    plan.close()
+    P = DeviceCSR(plan.nrows, B.ncols, rp, ci, None)
+    return DeviceCSR(plan.nrows, B.ncols, rp, ci, masked_semiring(A, B, P, semiring, dtype=dtype))
+
+
 def _plan_backward(self, a_vals, b_vals, dc_vals, need_a=True, need_b=True):
     """(dA, dB) for dC on this plan's C pattern (``spgemm_backward``)."""
     dev = self.workspace.device

@@ -642,14 +642,15 @@ spgemm_status spgemm_transpose(const spgemm_csr* M, int32_t dtype, int32_t* t_ro
   return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 
-spgemm_status spgemm_masked(const spgemm_csr* A, const spgemm_csr* B, const spgemm_csr* M, int32_t dtype,
-                            int32_t use_mask_values, void* c_vals, spgemm_stream_t stream) {
+static spgemm_status masked_impl(const spgemm_csr* A, const spgemm_csr* B, const spgemm_csr* M, int32_t dtype,
+                                 int32_t semiring, bool use_mask_values, void* c_vals, spgemm_stream_t stream) {
   spgemm_status s;
   if ((s = check_csr(A)) != SPGEMM_OK) return s;
   if ((s = check_csr(B)) != SPGEMM_OK) return s;
   if ((s = check_csr(M)) != SPGEMM_OK) return s;
   if (A->ncols != B->nrows || M->nrows != A->nrows || M->ncols != B->ncols) return SPGEMM_ERR_DIM_MISMATCH;
   if (dtype != SPGEMM_F64 && dtype != SPGEMM_F32) return SPGEMM_ERR_INVALID_ARG;
+  if (semiring < SPGEMM_PLUS_TIMES || semiring > SPGEMM_OR_AND) return SPGEMM_ERR_INVALID_ARG;
   if (M->nnz == 0) return SPGEMM_OK;
   if (!c_vals) return SPGEMM_ERR_INVALID_ARG;
   if ((A->nnz > 0 && !A->vals) || (B->nnz > 0 && !B->vals)) return SPGEMM_ERR_INVALID_ARG;
@@ -663,9 +664,19 @@ spgemm_status spgemm_masked(const spgemm_csr* A, const spgemm_csr* B, const spge
   const sg::Csr a{A->row_ptr, A->col_idx, A->nrows, A->ncols, A->nnz};
   const sg::Csr b{B->row_ptr, B->col_idx, B->nrows, B->ncols, B->nnz};
   const sg::Csr m{M->row_ptr, M->col_idx, M->nrows, M->ncols, M->nnz};
-  const cudaError_t e = sg::launch_masked(c, dtype, a, b, m, A->vals, B->vals, use_mask_values ? M->vals : nullptr,
-                                          c_vals);
+  const cudaError_t e = sg::launch_masked(c, dtype, semiring, a, b, m, A->vals, B->vals,
+                                          use_mask_values ? M->vals : nullptr, c_vals);
   return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
+}
+
+spgemm_status spgemm_masked(const spgemm_csr* A, const spgemm_csr* B, const spgemm_csr* M, int32_t dtype,
+                            int32_t use_mask_values, void* c_vals, spgemm_stream_t stream) {
+  return masked_impl(A, B, M, dtype, SPGEMM_PLUS_TIMES, use_mask_values != 0, c_vals, stream);
+}
+
+spgemm_status spgemm_semiring(const spgemm_csr* A, const spgemm_csr* B, const spgemm_csr* M, int32_t dtype,
+                              int32_t semiring, void* c_vals, spgemm_stream_t stream) {
+  return masked_impl(A, B, M, dtype, semiring, false, c_vals, stream);
 }
 
 spgemm_status spgemm_transpose_check(void* workspace, spgemm_stream_t stream) {

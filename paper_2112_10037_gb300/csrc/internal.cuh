@@ -284,9 +284,10 @@ cudaError_t launch_transpose(const LaunchCtx& c, long long m, long long n, long 
                              const int32_t* ci, int32_t* t_rp, int32_t* t_ci, int32_t* t_src, int32_t* fill,
                              int32_t* tmp_ci, int32_t* tmp_src, long long* partials);
 cudaError_t launch_gather(const LaunchCtx& c, int dtype, const void* v, const int32_t* src, void* out, long long nnz);
-// Masked product C<M> = (A*B) .* M on M's pattern (mv null: pattern only).
-cudaError_t launch_masked(const LaunchCtx& c, int dtype, const Csr& A, const Csr& B, const Csr& M, const void* av,
-                          const void* bv, const void* mv, void* out);
+// Masked product on M's pattern over a semiring (spgemm_semiring; 0 is
+// C<M> = (A*B) .* M, mv null for the pattern only; mv is unused otherwise).
+cudaError_t launch_masked(const LaunchCtx& c, int dtype, int semiring, const Csr& A, const Csr& B, const Csr& M,
+                          const void* av, const void* bv, const void* mv, void* out);
 cudaError_t launch_backward(const LaunchCtx& c, int dtype, const Csr& A, const Csr& B, long long row_begin,
                             long long mloc, const void* av, const void* bv, const int32_t* t_rp,
                             const int32_t* t_ci, const int32_t* t_src, const int32_t* c_rp,

@@ -52,7 +52,67 @@ __device__ __forceinline__ int find_in(const int32_t* __restrict__ ci, int lo, i
   return (lo < end && ci[lo] == j) ? lo : -1;
 }
 
-template <typename T>
+// Semirings (sum, product, zero): 0 plus-times (+, *, 0); 1 min-plus (min,
+// +, +inf); 2 max-plus (max, +, -inf); 3 or-and (or, both nonzero, 0 with
+// true written as 1).
+template <int SR, typename T>
+__device__ __forceinline__ T sr_zero() {
+  if (SR == 1) return T(INFINITY);
+  if (SR == 2) return T(-INFINITY);
+  return T(0);
+}
+
+template <int SR, typename T>
+__device__ __forceinline__ T sr_product(T a, T b) {
+  if (SR == 0) return a * b;
+  if (SR == 3) return (a != T(0) && b != T(0)) ? T(1) : T(0);
+  return a + b;
+}
+
+__device__ __forceinline__ unsigned long long to_bits(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ unsigned to_bits(float v) { return __float_as_uint(v); }
+__device__ __forceinline__ double from_bits(unsigned long long u) { return __longlong_as_double((long long)u); }
+__device__ __forceinline__ float from_bits(unsigned u) { return __uint_as_float(u); }
+
+// *p = min(*p, v) (MIN) or max(*p, v), shared or global memory, by
+// compare-and-swap on the bit pattern (no FP64 min/max atomics exist).  A
+// failed swap means another update improved the value first, so the loop
+// ends after at most as many rounds as there are updates of *p; the bound
+// is a guard that no input reaches.
+template <bool MIN, typename T>
+__device__ __forceinline__ void atomic_minmax(T* p, T v) {
+  using U = decltype(to_bits(v));
+  U* up = reinterpret_cast<U*>(p);
+  U old = *reinterpret_cast<volatile U*>(up);
+  for (int it = 0; it < CAS_RETRY_LIMIT; ++it) {
+    const T cur = from_bits(old);
+    if (MIN ? !(v < cur) : !(v > cur)) return;
+    const U prev = atomicCAS(up, old, to_bits(v));
+    if (prev == old) return;
+    old = prev;
+  }
+}
+
+// acc (+)= v in shared memory for semiring SR.
+template <int SR, typename T>
+__device__ __forceinline__ void sr_reduce_shared(T* p, T v) {
+  if (SR == 0) red_add_shared(p, v);
+  else if (SR == 1) atomic_minmax<true>(p, v);
+  else if (SR == 2) atomic_minmax<false>(p, v);
+  else if (v != T(0)) *p = T(1);  // every writer writes the same value
+}
+
+// out (+)= v in global memory for semiring SR; v equal to the zero is skipped.
+template <int SR, typename T>
+__device__ __forceinline__ void sr_reduce_global(T* p, T v) {
+  if (v == sr_zero<SR, T>()) return;
+  if (SR == 0) atomicAdd(p, v);
+  else if (SR == 1) atomic_minmax<true>(p, v);
+  else if (SR == 2) atomic_minmax<false>(p, v);
+  else *p = T(1);
+}
+
+template <typename T, int SR>
 __global__ void __launch_bounds__(MASK_WARPS * 32)
 k_masked(Csr A, Csr B, Csr M, const T* __restrict__ av, const T* __restrict__ bv, T* __restrict__ out) {
   __shared__ __align__(16) int s_col[MASK_WARPS][MASK_CAP];
@@ -84,7 +144,7 @@ k_masked(Csr A, Csr B, Csr M, const T* __restrict__ av, const T* __restrict__ bv
     if (staged) {
       for (int t = lane; t < m1 - m0; t += 32) {
         mc[t] = M.ci[m0 + t];
-        acc[t] = T(0);
+        acc[t] = sr_zero<SR, T>();
       }
       __syncwarp();
     }
@@ -109,19 +169,16 @@ k_masked(Csr A, Csr B, Csr M, const T* __restrict__ av, const T* __restrict__ bv
         const int j = B.ci[bi];
         if (staged) {
           const int p = (m1 > m0) ? find_in(mc, 0, m1 - m0, j) : -1;
-          if (p >= 0) red_add_shared(&acc[p], oa * bv[bi]);
+          if (p >= 0) sr_reduce_shared<SR>(&acc[p], sr_product<SR>(oa, bv[bi]));
         } else if (ohi > olo) {
           const int p = find_in(M.ci, olo, ohi, j);
-          if (p >= 0) atomicAdd(&out[p], oa * bv[bi]);
+          if (p >= 0) sr_reduce_global<SR>(&out[p], sr_product<SR>(oa, bv[bi]));
         }
       }
     }
     if (staged) {
       __syncwarp();
-      for (int t = lane; t < m1 - m0; t += 32) {
-        const T v = acc[t];
-        if (v != T(0)) atomicAdd(&out[m0 + t], v);
-      }
+      for (int t = lane; t < m1 - m0; t += 32) sr_reduce_global<SR>(&out[m0 + t], acc[t]);
       __syncwarp();
     }
   }
@@ -134,23 +191,52 @@ __global__ void __launch_bounds__(256) k_scale(T* __restrict__ out, const T* __r
     out[p] = out[p] * mv[p];
 }
 
-cudaError_t launch_masked(const LaunchCtx& c, int dtype, const Csr& A, const Csr& B, const Csr& M, const void* av,
-                          const void* bv, const void* mv, void* out) {
+// out[p] = the semiring's zero (+inf or -inf) for the nnz(M) entries.
+template <typename T, int SR>
+__global__ void __launch_bounds__(256) k_fill_zero(T* __restrict__ out, long long n) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x)
+    out[p] = sr_zero<SR, T>();
+}
+
+template <typename T, int SR>
+static cudaError_t masked_t(const LaunchCtx& c, const Csr& A, const Csr& B, const Csr& M, const T* av, const T* bv,
+                            const T* mv, T* out) {
+  const long long blocks = (M.nnz + 255) / 256;
+  const int eg = (int)(blocks < 4096 ? blocks : 4096);
+  cudaError_t e;
+  if (SR == 1 || SR == 2) {
+    k_fill_zero<T, SR><<<eg, 256, 0, c.stream>>>(out, M.nnz);
+    count_launch(c);
+    e = cudaGetLastError();
+  } else {
+    e = cudaMemsetAsync(out, 0, sizeof(T) * (size_t)M.nnz, c.stream);
+  }
+  if (e != cudaSuccess || A.nnz <= 0) return e;
+  auto k = k_masked<T, SR>;
+  const int occ = kernel_blocks_per_sm(k, MASK_WARPS * 32, 0);
+  const int grid = persistent_grid((A.nnz + 31) / 32, MASK_WARPS, c.nsm, occ);
+  k<<<grid, MASK_WARPS * 32, 0, c.stream>>>(A, B, M, av, bv, out);
+  count_launch(c);
+  if ((e = cudaGetLastError()) != cudaSuccess || SR != 0 || !mv) return e;
+  k_scale<T><<<eg, 256, 0, c.stream>>>(out, mv, M.nnz);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_masked(const LaunchCtx& c, int dtype, int semiring, const Csr& A, const Csr& B, const Csr& M,
+                          const void* av, const void* bv, const void* mv, void* out) {
   if (M.nrows <= 0 || M.nnz <= 0) return cudaSuccess;
   auto run = [&](auto* tag) -> cudaError_t {
     using T = std::remove_pointer_t<decltype(tag)>;
-    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(T) * (size_t)M.nnz, c.stream);
-    if (e != cudaSuccess || A.nnz <= 0) return e;
-    auto k = k_masked<T>;
-    const int occ = kernel_blocks_per_sm(k, MASK_WARPS * 32, 0);
-    const int grid = persistent_grid((A.nnz + 31) / 32, MASK_WARPS, c.nsm, occ);
-    k<<<grid, MASK_WARPS * 32, 0, c.stream>>>(A, B, M, (const T*)av, (const T*)bv, (T*)out);
-    count_launch(c);
-    if ((e = cudaGetLastError()) != cudaSuccess || !mv) return e;
-    const long long blocks = (M.nnz + 255) / 256;
-    k_scale<T><<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, c.stream>>>((T*)out, (const T*)mv, M.nnz);
-    count_launch(c);
-    return cudaGetLastError();
+    const T* a = (const T*)av;
+    const T* b = (const T*)bv;
+    T* o = (T*)out;
+    switch (semiring) {
+      case 1: return masked_t<T, 1>(c, A, B, M, a, b, nullptr, o);
+      case 2: return masked_t<T, 2>(c, A, B, M, a, b, nullptr, o);
+      case 3: return masked_t<T, 3>(c, A, B, M, a, b, nullptr, o);
+      default: return masked_t<T, 0>(c, A, B, M, a, b, (const T*)mv, o);
+    }
   };
   return dtype == SPGEMM_F32 ? run((float*)nullptr) : run((double*)nullptr);
 }
