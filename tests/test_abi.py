@@ -70,3 +70,34 @@ def test_host_checks_without_gpu(libpath):
     assert nat.spgemm_version().count(".") == 2
     for s in range(10):
         assert nat.spgemm_status_string(s)
+
+
+def test_masked_and_semiring_host_checks_without_gpu(libpath):
+    """Argument checks of spgemm_masked / spgemm_semiring happen on the host
+    before any device work: shape mismatch, unknown semiring or dtype, a
+    missing output; an empty mask is a no-op."""
+    def csr(m, n, nnz=0):
+        s = nat.spgemm_csr()
+        s.nrows, s.ncols, s.nnz = m, n, nnz
+        s.row_ptr = 16  # never dereferenced on the host
+        s.col_idx = 16 if nnz else 0
+        s.vals = 16 if nnz else 0
+        return s
+    A, B = csr(5, 4), csr(4, 6)
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_masked(A, B, csr(5, 7), nat.SPGEMM_F64, True, 0, 0)
+    assert ei.value.status == 2
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_semiring(A, B, csr(6, 6), nat.SPGEMM_F64, nat.SPGEMM_MIN_PLUS, 0, 0)
+    assert ei.value.status == 2
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_semiring(A, B, csr(5, 6), nat.SPGEMM_F64, 9, 0, 0)
+    assert ei.value.status == 1
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_semiring(A, B, csr(5, 6), 7, nat.SPGEMM_OR_AND, 0, 0)
+    assert ei.value.status == 1
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_masked(A, B, csr(5, 6, 3), nat.SPGEMM_F64, False, 0, 0)  # output missing
+    assert ei.value.status == 1
+    nat.spgemm_masked(A, B, csr(5, 6), nat.SPGEMM_F64, False, 0, 0)      # empty mask: nothing to do
+    nat.spgemm_semiring(A, B, csr(5, 6), nat.SPGEMM_F32, nat.SPGEMM_MAX_PLUS, 0, 0)
