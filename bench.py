@@ -760,6 +760,43 @@ def run_omar(args):
     return out
 
 
+def run_variants(args):
+    """The widened products on the 3D stencil 96^3 (A*A) and on R-MAT
+    scale 16 (A*A): the column-wise Gustavson product (transposes around a
+    row-wise product, all three steps timed), and the semiring values
+    (min-plus, max-plus, or-and) on the pattern of A*B, timed without the
+    pattern's own computation.  GFLOP/s counts 2 FLOP per product formed."""
+    import torch
+    from paper_2112_10037_gb300 import api, build as bld
+    bld.build()
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, M in (("laplacian3d_96", gen.laplacian_3d(96)), ("rmat_s16_ef16", gen.rmat(16, 16))):
+        products = int(row_products(M, M).sum())
+        dM = api.DeviceCSR.from_host(M)
+        entry = {"products": products}
+        for _ in range(args.warmup):
+            api.spgemm_colwise(dM, dM)
+        ms, _ = _events_ms(lambda: api.spgemm_colwise(dM, dM), args.steps, stream)
+        entry["colwise"] = {"ms": round(ms, 4), "gflops": round(2.0 * products / (ms / 1e3) / 1e9, 2)}
+        ms_row, _ = _events_ms(lambda: api.spgemm(dM, dM), args.steps, stream)
+        entry["rowwise"] = {"ms": round(ms_row, 4), "gflops": round(2.0 * products / (ms_row / 1e3) / 1e9, 2)}
+        C = api.spgemm(dM, dM)
+        P = api.DeviceCSR(C.nrows, C.ncols, C.row_ptr, C.col_idx, None)
+        for sr in ("min_plus", "max_plus", "or_and"):
+            for _ in range(args.warmup):
+                api.masked_semiring(dM, dM, P, sr)
+            ms, _ = _events_ms(lambda: api.masked_semiring(dM, dM, P, sr), args.steps, stream)
+            entry[sr] = {"ms": round(ms, 4), "gflops": round(2.0 * products / (ms / 1e3) / 1e9, 2)}
+        res[name] = entry
+    first = res["laplacian3d_96"]
+    out = _base_line("SpGEMM GFLOP/s (2*products/s), min-plus values on the product's pattern",
+                     first["min_plus"]["gflops"], "GFLOP/s", args, first["min_plus"]["ms"],
+                     {"workload": "variants_laplacian3d_96_and_rmat_s16"})
+    out["matrices"] = res
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -767,7 +804,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat",
-                    choices=["rmat", "lap2d", "stencil3d", "batched", "galerkin", "backward", "triangles", "omar"])
+                    choices=["rmat", "lap2d", "stencil3d", "batched", "galerkin", "backward", "triangles", "omar",
+                             "variants"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-scale", type=float, default=0.1,
                     help="row-count scale of the batched instances (1.0 = rows in [1024, 200000])")
@@ -790,10 +828,10 @@ def main():
         A, B, desc = make_workload(args.workload, args.rmat_scale)
         print(json.dumps(run_reference(args, A, B, desc)), flush=True)
         return
-    if args.workload in ("batched", "galerkin", "backward", "triangles", "omar"):
+    if args.workload in ("batched", "galerkin", "backward", "triangles", "omar", "variants"):
         if rank == 0:
             runner = {"batched": run_batched, "galerkin": run_galerkin, "backward": run_backward,
-                      "triangles": run_triangles, "omar": run_omar}[args.workload]
+                      "triangles": run_triangles, "omar": run_omar, "variants": run_variants}[args.workload]
             print(json.dumps(runner(args)), flush=True)
         return
     if world > 1:

@@ -8,7 +8,7 @@
 //     its source row (the new column index) and its source position,
 //  4. sort each output row by source row (unique within a column): up to 32
 //     entries in registers, up to 8192 entries by a block in shared memory,
-//     longer rows by counting, for each entry, the smaller keys of its row,
+//     longer rows through a shared-memory bitmap over their key range,
 //  5. optionally gather the values through the source positions.
 // The source positions let a caller move new values of the same structure
 // (t_v[q] = v[t_src[q]]) without transposing again.
@@ -131,25 +131,97 @@ __global__ void __launch_bounds__(1024) k_t_sort_mid(const int32_t* __restrict__
   }
 }
 
-// Rows longer than 8192 entries: each entry's rank is the number of smaller
-// keys in its row (keys are distinct); entries are written to a scratch copy
-// at their rank, then copied back.  Quadratic in the row length, used only
-// for very long columns.
-__global__ void __launch_bounds__(512) k_t_sort_long(const int32_t* __restrict__ t_rp, long long n,
-                                                     int32_t* __restrict__ t_ci, int32_t* __restrict__ t_src,
-                                                     int32_t* __restrict__ tmp_ci, int32_t* __restrict__ tmp_src) {
+// Rows longer than 8192 entries (long columns of M): the row's keys (its
+// source rows, distinct) are marked in a shared-memory bitmap, one window of
+// T_BITS_WORDS * 32 keys at a time over the row's key range; a block-wide
+// prefix sum of the window's per-word popcounts gives every marked key its
+// rank, and the keys are written in ascending order to the scratch copy.
+// Each key's source position is found again by a binary search for this
+// column in the key's row of M (M's rows are sorted).  The scratch copy is
+// then copied back.  Work per row: its entries, each with one binary search,
+// plus its key span / 32 bitmap words.
+constexpr int T_BITS_WORDS = 8192;   // 262,144 keys per window (32 KB)
+constexpr int T_LONG_THREADS = 1024;
+
+__global__ void __launch_bounds__(T_LONG_THREADS) k_t_sort_long(const int32_t* __restrict__ rp,
+                                                                const int32_t* __restrict__ ci,
+                                                                const int32_t* __restrict__ t_rp, long long n,
+                                                                int32_t* __restrict__ t_ci, int32_t* __restrict__ t_src,
+                                                                int32_t* __restrict__ tmp_ci,
+                                                                int32_t* __restrict__ tmp_src) {
+  constexpr int WPT = T_BITS_WORDS / T_LONG_THREADS;  // bitmap words per thread
+  constexpr int NWARP = T_LONG_THREADS / 32;
+  static_assert(NWARP == 32, "one warp scans the warp totals");
+  __shared__ uint32_t bits[T_BITS_WORDS];
+  __shared__ int s_warp[NWARP];
+  __shared__ int s_kmin, s_kmax;
+  const int tid = threadIdx.x, lane = lane_id(), warp = tid >> 5;
   for (long long r = blockIdx.x; r < n; r += gridDim.x) {
     const int b = t_rp[r], len = t_rp[r + 1] - b;
-    if (len <= T_SMEM_SORT) continue;
-    for (int x = threadIdx.x; x < len; x += blockDim.x) {
-      const int kx = t_ci[b + x];
-      int rank = 0;
-      for (int y = 0; y < len; ++y) rank += t_ci[b + y] < kx;
-      tmp_ci[b + rank] = kx;
-      tmp_src[b + rank] = t_src[b + x];
+    if (len <= T_SMEM_SORT) continue;  // the same for the whole block
+    int mn = INT_MAX, mx = -1;
+    for (int x = tid; x < len; x += T_LONG_THREADS) {
+      const int k = t_ci[b + x];
+      mn = min(mn, k);
+      mx = max(mx, k);
+    }
+    mn = warp_min(mn);
+    mx = warp_max(mx);
+    if (tid == 0) {
+      s_kmin = INT_MAX;
+      s_kmax = -1;
     }
     __syncthreads();
-    for (int x = threadIdx.x; x < len; x += blockDim.x) {
+    if (lane == 0) {
+      atomicMin(&s_kmin, mn);
+      atomicMax(&s_kmax, mx);
+    }
+    __syncthreads();
+    const int kmin = s_kmin, kmax = s_kmax;
+    int done = 0;  // keys placed by earlier windows
+    for (long long w0 = kmin & ~31; w0 <= kmax; w0 += 32LL * T_BITS_WORDS) {
+      for (int t = tid; t < T_BITS_WORDS; t += T_LONG_THREADS) bits[t] = 0u;
+      __syncthreads();
+      for (int x = tid; x < len; x += T_LONG_THREADS) {
+        const long long d = (long long)t_ci[b + x] - w0;
+        if (d >= 0 && d < 32LL * T_BITS_WORDS) atomicOr(&bits[d >> 5], 1u << (d & 31));
+      }
+      __syncthreads();
+      uint32_t wv[WPT];
+      int cnt = 0;
+#pragma unroll
+      for (int u = 0; u < WPT; ++u) {
+        wv[u] = bits[tid * WPT + u];
+        cnt += __popc(wv[u]);
+      }
+      const int incl = warp_incl_scan(cnt);
+      if (lane == 31) s_warp[warp] = incl;
+      __syncthreads();
+      if (warp == 0) s_warp[lane] = warp_incl_scan(s_warp[lane]);
+      __syncthreads();
+      int pos = done + (warp > 0 ? s_warp[warp - 1] : 0) + incl - cnt;
+      const int total = s_warp[NWARP - 1];
+#pragma unroll
+      for (int u = 0; u < WPT; ++u) {
+        uint32_t v = wv[u];
+        while (v) {
+          const int bit = __ffs(v) - 1;
+          v &= v - 1;
+          const int key = (int)(w0 + 32LL * (tid * WPT + u) + bit);
+          int lo = rp[key], hi = rp[key + 1];  // column r lies in row `key` of M
+          while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (ci[mid] < (int)r) lo = mid + 1; else hi = mid;
+          }
+          tmp_ci[b + pos] = key;
+          tmp_src[b + pos] = lo;
+          ++pos;
+        }
+      }
+      done += total;
+      __syncthreads();  // bits and s_warp are reused by the next window
+    }
+    for (int x = tid; x < len; x += T_LONG_THREADS) {
       t_ci[b + x] = tmp_ci[b + x];
       t_src[b + x] = tmp_src[b + x];
     }
@@ -192,7 +264,8 @@ cudaError_t launch_transpose(const LaunchCtx& c, long long m, long long n, long 
   if (kernel_blocks_per_sm(k_t_sort_mid, 1024, mid_smem) <= 0) return cudaErrorInvalidConfiguration;
   k_t_sort_mid<<<grid_cap(n, 1, c.nsm, 2), 1024, mid_smem, c.stream>>>(t_rp, n, t_ci, t_src);
   count_launch(c);
-  k_t_sort_long<<<grid_cap(n, 1, c.nsm, 2), 512, 0, c.stream>>>(t_rp, n, t_ci, t_src, tmp_ci, tmp_src);
+  k_t_sort_long<<<grid_cap(n, 1, c.nsm, 2), T_LONG_THREADS, 0, c.stream>>>(rp, ci, t_rp, n, t_ci, t_src, tmp_ci,
+                                                                            tmp_src);
   count_launch(c);
   return cudaGetLastError();
 }
