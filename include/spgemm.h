@@ -238,8 +238,11 @@ spgemm_status spgemm_transpose_workspace_size(int64_t nrows, int64_t ncols, int6
 /* M^T in CSR (Sec. 2.1: M's CSC form): t_row_ptr (ncols+1 entries),
  * t_col_idx (nnz; each row ascending), t_vals (nnz values of `dtype`, or NULL
  * for structure only), t_src (nnz source positions in M, or NULL), so that
- * t_vals[q] = M.vals[t_src[q]].  Column indices of M must be in range.
- * Does not block; spgemm_transpose_check reads the error word. */
+ * t_vals[q] = M.vals[t_src[q]].  Column indices of M must be in range and,
+ * as for every input of this library, ascending and unique within each row
+ * (columns of M with more than 8192 entries rely on it).  Does not block;
+ * spgemm_transpose_check reads the error word: SPGEMM_ERR_UNSORTED_INPUT for
+ * a column index out of range or a repeated column found in a long column. */
 spgemm_status spgemm_transpose(const spgemm_csr* M, int32_t dtype, int32_t* t_row_ptr, int32_t* t_col_idx,
                                void* t_vals, int32_t* t_src, void* workspace, size_t workspace_bytes,
                                spgemm_stream_t stream);
@@ -258,8 +261,10 @@ spgemm_status spgemm_transpose_check(void* workspace, spgemm_stream_t stream);
  * Its scratch is one fixed 8 MiB device array inside this library, present
  * on every GPU that loads the library until the process exits.  Inputs whose
  * scratch would exceed it are rejected with SPGEMM_ERR_WORKSPACE: the need
- * is about 4*nnz (12*nnz when t_src is NULL) + 4*ncols + 8*ncols/4096 bytes
- * plus a few hundred bytes of bookkeeping.  The first call on a device looks
+ * is 8*nnz bytes (12*nnz when t_src is NULL, which then also needs scratch)
+ * + 4*ncols + 8*ncols/4096 bytes plus about 2 KB of bookkeeping and
+ * alignment, so about 1 M entries fit with t_src given.  The inputs follow
+ * spgemm_transpose's preconditions.  The first call on a device looks
  * up the array's device address; make that first call before any stream
  * capture.  All calls on a device share the array (each call clears what
  * must start at zero), so calls whose GPU work can overlap -- on different
@@ -357,6 +362,33 @@ spgemm_status spgemm_batch_symbolic(spgemm_batch* batch, int32_t* c_row_ptr, int
  * values.  Does not block and allocates nothing: capturable in a CUDA graph. */
 spgemm_status spgemm_batch_numeric(spgemm_batch* batch, const int32_t* c_row_ptr, int32_t* c_col_idx,
                                    void* c_vals, spgemm_stream_t stream);
+
+/* Same types as cudaGraph_t and cudaGraphExec_t. */
+typedef struct CUgraph_st* spgemm_graph_t;
+typedef struct CUgraphExec_st* spgemm_graph_exec_t;
+
+/* Records the batch numeric pass (spgemm_batch_numeric with these output
+ * arrays) into a new CUDA graph, which *graph receives and the caller owns
+ * (spgemm_graph_destroy or cudaGraphDestroy).  The batched launch of the
+ * spec workloads is meant to run this way: instantiate once, then
+ * launch the graph for every new set of values written in place into the
+ * instances' value buffers.  The graph reads the value buffers given to
+ * spgemm_batched and writes c_col_idx / c_vals; all of them must stay valid
+ * while the graph can run.  spgemm_batch_symbolic must have run
+ * (SPGEMM_ERR_NOT_READY otherwise).  `stream` is used for the capture only:
+ * it must be a stream the caller created (not the legacy default stream,
+ * SPGEMM_ERR_INVALID_ARG) that is not already capturing; the capture is in
+ * thread-local mode and issues no GPU work.  Does not block. */
+spgemm_status spgemm_batch_capture(spgemm_batch* batch, const int32_t* c_row_ptr, int32_t* c_col_idx,
+                                   void* c_vals, spgemm_stream_t stream, spgemm_graph_t* graph);
+
+/* Graph helpers for callers without the CUDA runtime API at hand (thin
+ * wrappers of cudaGraphInstantiate, cudaGraphLaunch, cudaGraphExecDestroy
+ * and cudaGraphDestroy).  spgemm_graph_launch is asynchronous on `stream`;
+ * spgemm_graph_destroy accepts NULL for either argument. */
+spgemm_status spgemm_graph_instantiate(spgemm_graph_t graph, spgemm_graph_exec_t* exec);
+spgemm_status spgemm_graph_launch(spgemm_graph_exec_t exec, spgemm_stream_t stream);
+void spgemm_graph_destroy(spgemm_graph_t graph, spgemm_graph_exec_t exec);
 
 /* The plan of the stacked product (statistics, timers, error word). */
 spgemm_plan* spgemm_batch_plan(spgemm_batch* batch);

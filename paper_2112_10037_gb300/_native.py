@@ -92,6 +92,10 @@ _SIG = {
     "spgemm_batch_rows": ([_P, _I64P], ctypes.c_int),
     "spgemm_batch_symbolic": ([_P, _P, _I64P, _P], ctypes.c_int),
     "spgemm_batch_numeric": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "spgemm_batch_capture": ([_P, _P, _P, _P, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "spgemm_graph_instantiate": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
+    "spgemm_graph_launch": ([_P, _P], ctypes.c_int),
+    "spgemm_graph_destroy": ([_P, _P], None),
     "spgemm_batch_plan": ([_P], _P),
     "spgemm_batch_destroy": ([_P], None),
 }
@@ -278,6 +282,28 @@ def spgemm_batch_symbolic(batch: int, n: int, c_row_ptr: int, stream: int):
 def spgemm_batch_numeric(batch: int, c_row_ptr: int, c_col_idx: int, c_vals: int, stream: int) -> None:
     _check(lib().spgemm_batch_numeric(_P(batch), _P(c_row_ptr), _P(c_col_idx), _P(c_vals), _P(stream)),
            "spgemm_batch_numeric")
+
+
+def spgemm_batch_capture(batch: int, c_row_ptr: int, c_col_idx: int, c_vals: int, stream: int) -> int:
+    """Handle of a new CUDA graph holding the batch numeric pass."""
+    g = _P(None)
+    _check(lib().spgemm_batch_capture(_P(batch), _P(c_row_ptr), _P(c_col_idx), _P(c_vals), _P(stream),
+                                      ctypes.byref(g)), "spgemm_batch_capture")
+    return g.value
+
+
+def spgemm_graph_instantiate(graph: int) -> int:
+    ge = _P(None)
+    _check(lib().spgemm_graph_instantiate(_P(graph), ctypes.byref(ge)), "spgemm_graph_instantiate")
+    return ge.value
+
+
+def spgemm_graph_launch(exec_: int, stream: int) -> None:
+    _check(lib().spgemm_graph_launch(_P(exec_), _P(stream)), "spgemm_graph_launch")
+
+
+def spgemm_graph_destroy(graph: int, exec_: int) -> None:
+    lib().spgemm_graph_destroy(_P(graph), _P(exec_))
 
 
 def spgemm_batch_plan(batch: int) -> int:

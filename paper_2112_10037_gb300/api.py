@@ -525,22 +525,25 @@ class Batch:
                                  self.vals.data_ptr() if self.nnz[-1] else 0, self.stream)
 
     def capture(self):
-        """Record numeric() in a CUDA graph (after one eager numeric())."""
-        g = torch.cuda.CUDAGraph()
+        """Record numeric() in a CUDA graph through ``spgemm_batch_capture``
+        (after symbolic()); ``replay()`` launches it on the current stream."""
+        if self.row_ptr is None:
+            self.symbolic()
+        self._drop_graph()
         s = torch.cuda.Stream(device=self.device)
-        s.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(s):
-            saved = self.stream
-            self.stream = int(s.cuda_stream)
-            with torch.cuda.graph(g, stream=s):
-                self.numeric()
-            self.stream = saved
-        torch.cuda.current_stream().wait_stream(s)
-        self.graph = g
-        return g
+        g = nat.spgemm_batch_capture(self.handle, self.row_ptr.data_ptr(),
+                                     self.col_idx.data_ptr() if self.nnz[-1] else 0,
+                                     self.vals.data_ptr() if self.nnz[-1] else 0, int(s.cuda_stream))
+        self.graph = (g, nat.spgemm_graph_instantiate(g))
+        return self.graph
 
-    def replay(self):
-        self.graph.replay()
+    def replay(self, stream=None):
+        nat.spgemm_graph_launch(self.graph[1], _stream_handle(stream))
+
+    def _drop_graph(self):
+        if getattr(self, "graph", None):
+            nat.spgemm_graph_destroy(*self.graph)
+            self.graph = None
 
     def results(self):
         out, r0, e0 = [], 0, 0
@@ -555,6 +558,7 @@ class Batch:
         return nat.spgemm_batch_plan(self.handle)
 
     def close(self):
+        self._drop_graph()
         if getattr(self, "handle", None):
             nat.spgemm_batch_destroy(self.handle)
             self.handle = None

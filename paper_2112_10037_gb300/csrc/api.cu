@@ -868,6 +868,48 @@ spgemm_status spgemm_batch_numeric(spgemm_batch* b, const int32_t* c_row_ptr, in
   return SPGEMM_OK;
 }
 
+spgemm_status spgemm_batch_capture(spgemm_batch* b, const int32_t* c_row_ptr, int32_t* c_col_idx, void* c_vals,
+                                   spgemm_stream_t stream, spgemm_graph_t* graph) {
+  if (!b || !c_row_ptr || !graph || !stream) return SPGEMM_ERR_INVALID_ARG;
+  *graph = nullptr;
+  if (!b->plan->symbolic_done) return SPGEMM_ERR_NOT_READY;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  if (cs != cudaStreamCaptureStatusNone) return SPGEMM_ERR_INVALID_ARG;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  spgemm_status s = spgemm_batch_numeric(b, c_row_ptr, c_col_idx, c_vals, stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (s != SPGEMM_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return s != SPGEMM_OK ? s : SPGEMM_ERR_CUDA;
+  }
+  *graph = (spgemm_graph_t)g;
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_graph_instantiate(spgemm_graph_t graph, spgemm_graph_exec_t* exec) {
+  if (!graph || !exec) return SPGEMM_ERR_INVALID_ARG;
+  cudaGraphExec_t ge = nullptr;
+  if (cudaGraphInstantiate(&ge, (cudaGraph_t)graph, 0) != cudaSuccess) {
+    *exec = nullptr;
+    return SPGEMM_ERR_CUDA;
+  }
+  *exec = (spgemm_graph_exec_t)ge;
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_graph_launch(spgemm_graph_exec_t exec, spgemm_stream_t stream) {
+  if (!exec) return SPGEMM_ERR_INVALID_ARG;
+  return cudaGraphLaunch((cudaGraphExec_t)exec, (cudaStream_t)stream) == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
+}
+
+void spgemm_graph_destroy(spgemm_graph_t graph, spgemm_graph_exec_t exec) {
+  if (exec) cudaGraphExecDestroy((cudaGraphExec_t)exec);
+  if (graph) cudaGraphDestroy((cudaGraph_t)graph);
+}
+
 spgemm_plan* spgemm_batch_plan(spgemm_batch* b) { return b ? b->plan : nullptr; }
 
 void spgemm_batch_destroy(spgemm_batch* b) { delete b; }

@@ -35,11 +35,13 @@ struct NaLayout {
   size_t st, src, fill, tmp, part, total;
 };
 
-NaLayout na_layout(long long ncols, long long nnz) {
+// The source positions get scratch only when the caller passes no t_src.
+NaLayout na_layout(long long ncols, long long nnz, bool need_src) {
   NaLayout L{};
   size_t off = 0;
   L.st = off; off = na_align(off + sizeof(DevStats));
-  L.src = off; off = na_align(off + sizeof(int32_t) * (size_t)nnz);
+  L.src = off;
+  if (need_src) off = na_align(off + sizeof(int32_t) * (size_t)nnz);
   L.fill = off; off = na_align(off + sizeof(int32_t) * (size_t)(ncols > 0 ? ncols : 1));
   L.tmp = off; off = na_align(off + 2 * sizeof(int32_t) * (size_t)nnz);
   L.part = off; off = na_align(off + sizeof(long long) * scan_partials_count(ncols));
@@ -86,7 +88,7 @@ extern "C" spgemm_status spgemm_transpose_noalloc(const spgemm_csr* M, int32_t d
   if (!t_row_ptr || (M->nnz > 0 && !t_col_idx)) return SPGEMM_ERR_INVALID_ARG;
   if (dtype != SPGEMM_F64 && dtype != SPGEMM_F32) return SPGEMM_ERR_INVALID_ARG;
   if (t_vals && M->nnz > 0 && !M->vals) return SPGEMM_ERR_INVALID_ARG;
-  const NaLayout L = na_layout(M->ncols, M->nnz);
+  const NaLayout L = na_layout(M->ncols, M->nnz, t_src == nullptr);
   if (L.total > NOALLOC_SCRATCH_BYTES) return SPGEMM_ERR_WORKSPACE;  // does not fit the fixed scratch
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SPGEMM_ERR_CUDA;

@@ -139,7 +139,9 @@ __global__ void __launch_bounds__(1024) k_t_sort_mid(const int32_t* __restrict__
 // Each key's source position is found again by a binary search for this
 // column in the key's row of M (M's rows are sorted).  The scratch copy is
 // then copied back.  Work per row: its entries, each with one binary search,
-// plus its key span / 32 bitmap words.
+// plus its key span / 32 bitmap words.  This needs M's rows ascending and
+// without repeated columns (the library's input precondition); a repeated
+// column leaves fewer keys than entries and is reported as unsorted input.
 constexpr int T_BITS_WORDS = 8192;   // 262,144 keys per window (32 KB)
 constexpr int T_LONG_THREADS = 1024;
 
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(T_LONG_THREADS) k_t_sort_long(const int32_t* _
                                                                 const int32_t* __restrict__ t_rp, long long n,
                                                                 int32_t* __restrict__ t_ci, int32_t* __restrict__ t_src,
                                                                 int32_t* __restrict__ tmp_ci,
-                                                                int32_t* __restrict__ tmp_src) {
+                                                                int32_t* __restrict__ tmp_src, uint32_t* err) {
   constexpr int WPT = T_BITS_WORDS / T_LONG_THREADS;  // bitmap words per thread
   constexpr int NWARP = T_LONG_THREADS / 32;
   static_assert(NWARP == 32, "one warp scans the warp totals");
@@ -221,6 +223,9 @@ __global__ void __launch_bounds__(T_LONG_THREADS) k_t_sort_long(const int32_t* _
       done += total;
       __syncthreads();  // bits and s_warp are reused by the next window
     }
+    // a repeated column in a row of M marks one bit for two entries, so fewer
+    // keys than entries were placed (the rest of the row was not written)
+    if (tid == 0 && done != len) atomicOr(err, EB_UNSORTED);
     for (int x = tid; x < len; x += T_LONG_THREADS) {
       t_ci[b + x] = tmp_ci[b + x];
       t_src[b + x] = tmp_src[b + x];
@@ -265,7 +270,7 @@ cudaError_t launch_transpose(const LaunchCtx& c, long long m, long long n, long 
   k_t_sort_mid<<<grid_cap(n, 1, c.nsm, 2), 1024, mid_smem, c.stream>>>(t_rp, n, t_ci, t_src);
   count_launch(c);
   k_t_sort_long<<<grid_cap(n, 1, c.nsm, 2), T_LONG_THREADS, 0, c.stream>>>(rp, ci, t_rp, n, t_ci, t_src, tmp_ci,
-                                                                            tmp_src);
+                                                                            tmp_src, c.err);
   count_launch(c);
   return cudaGetLastError();
 }

@@ -76,3 +76,46 @@ def load_golden(path):
         v = np.array([x for r in d["rows"] for _, x in r], np.float64)
         out[name] = gen.CSR(d["m"], d["n"], rp, ci, v)
     return out
+
+
+def stencil3d_square_closed_form(n, rp, ci):
+    """Expected values of A*A for the 3D 7-point operator (6 on the
+    diagonal, -1 to each face neighbour, Dirichlet) on an n^3 grid, from the
+    offset between row and column: 36 + deg(i) on the diagonal (deg = the
+    row's face neighbours, 6 in the interior), -12 at distance 1, 2 at the
+    diagonal offsets (two paths), 1 at distance 2 along an axis; nnz is the
+    sum over the 25 offsets of the in-grid positions."""
+    rp = np.asarray(rp, np.int64)
+    rows = np.repeat(np.arange(n ** 3, dtype=np.int64), np.diff(rp))
+    cols = np.asarray(ci, np.int64)
+    def coords(x):
+        return x // (n * n), (x // n) % n, x % n
+    zi, yi, xi = coords(rows)
+    zj, yj, xj = coords(cols)
+    d = np.abs(zi - zj) + np.abs(yi - yj) + np.abs(xi - xj)
+    axis = (zi == zj).astype(int) + (yi == yj) + (xi == xj)
+    deg = sum(((c > 0).astype(np.int64) + (c < n - 1)) for c in (zi, yi, xi))
+    exp = np.full(len(rows), np.nan)
+    exp[d == 0] = 36 + deg[d == 0]
+    exp[d == 1] = -12
+    exp[(d == 2) & (axis == 1)] = 2   # two coordinates differ by one
+    exp[(d == 2) & (axis == 2)] = 1   # one coordinate differs by two
+    return exp
+
+
+def long_column_matrix(m=600_000, every=50, seed=6):
+    """Column 0 set in every `every`-th row (12,000 entries over 600,000
+    source rows, so its transpose row spans more than one 262,144-key
+    window of the long-row sort), plus one random column in [1, 64) in every
+    third row."""
+    rng = np.random.default_rng(seed)
+    i = np.arange(m)
+    c0 = i % every == 0
+    c1 = i % 3 == 0
+    other = rng.integers(1, 64, size=m)
+    counts = c0.astype(np.int64) + c1
+    rp = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    ci = np.empty(int(rp[-1]), np.int32)
+    ci[rp[:-1][c0]] = 0
+    ci[(rp[1:] - 1)[c1]] = other[c1]
+    return gen.CSR(m, 64, rp, ci, rng.standard_normal(len(ci))).check()

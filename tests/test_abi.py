@@ -101,3 +101,18 @@ def test_masked_and_semiring_host_checks_without_gpu(libpath):
     assert ei.value.status == 1
     nat.spgemm_masked(A, B, csr(5, 6), nat.SPGEMM_F64, False, 0, 0)      # empty mask: nothing to do
     nat.spgemm_semiring(A, B, csr(5, 6), nat.SPGEMM_F32, nat.SPGEMM_MAX_PLUS, 0, 0)
+
+
+def test_graph_calls_host_checks_without_gpu(libpath):
+    """spgemm_batch_capture and the graph helpers reject missing handles on
+    the host, before any CUDA call."""
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_batch_capture(0, 16, 16, 16, 16)
+    assert ei.value.status == 1
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_graph_instantiate(0)
+    assert ei.value.status == 1
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_graph_launch(0, 0)
+    assert ei.value.status == 1
+    nat.spgemm_graph_destroy(0, 0)  # NULL handles: nothing to free

@@ -56,6 +56,9 @@ def test_batch_matches_oracle_and_single_calls(api, oracle_mod):
 
 
 def test_batch_graph_replay_new_values(api, oracle_mod):
+    """The batch numeric pass recorded by spgemm_batch_capture (the C ABI's
+    capture call) and launched three times with new values written in
+    place into the instances' value buffers."""
     insts = [i for i in _small_batch(10, 0.01)]
     pairs = [(api.DeviceCSR.from_host(i.A), api.DeviceCSR.from_host(i.B)) for i in insts]
     batch = api.Batch(pairs)

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2112_10037_gb300 import gen
-from parity import RTOL_F32, assert_structure_equal, max_rel_err
+from parity import RTOL_F32, assert_structure_equal, long_column_matrix, max_rel_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -54,6 +54,32 @@ def test_transpose_long_columns(api, oracle_mod):
     got = T.to_host()
     assert_structure_equal(got, R)
     assert np.array_equal(got.vals, R.vals)
+
+
+def test_transpose_long_column_spanning_windows(api, oracle_mod):
+    M = long_column_matrix()
+    T, src = api.transpose(api.DeviceCSR.from_host(M), want_src=True)
+    R = oracle_mod.transpose(M)
+    got = T.to_host()
+    assert_structure_equal(got, R)
+    assert np.array_equal(got.vals, R.vals)
+    assert np.array_equal(M.vals[src.cpu().numpy()], R.vals)
+    assert int(np.diff(R.row_ptr)[0]) == 12_000
+
+
+def test_transpose_repeated_column_in_long_column_is_reported(api):
+    """A row of M that repeats a column breaks the input precondition; in a
+    column of more than 8192 entries the transpose reports it as unsorted
+    input instead of returning a row with unwritten entries."""
+    m = 9000
+    rows = [np.array([0, 0, 5]) if i == 17 else np.array([0, 1 + i % 7]) for i in range(m)]
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    ci = np.concatenate(rows).astype(np.int32)
+    M = gen.CSR(m, 8, rp, ci, np.ones(len(ci)))
+    from paper_2112_10037_gb300 import _native as nat
+    with pytest.raises(nat.SpgemmError) as ei:
+        api.transpose(api.DeviceCSR.from_host(M))
+    assert ei.value.status == 3
 
 
 def _grad_oracle(oracle_mod, A, B, W):

@@ -217,6 +217,32 @@ def test_laplacian3d_squared_diagonal(oracle_mod):
     assert np.array_equal(np.diag(d), 36.0 + deg)
 
 
+@pytest.mark.parametrize("n", [1, 2, 3, 8])
+def test_laplacian3d_squared_closed_form(oracle_mod, n):
+    """A*A for the 3D 7-point operator against its closed form entry by
+    entry (36 + deg on the diagonal, -12 at distance 1, 2 at diagonal
+    offsets, 1 at distance-2 axial offsets; the same helper checks the
+    device's 96^3 product)."""
+    from parity import stencil3d_square_closed_form
+    A = gen.laplacian_3d(n)
+    C = oracle_mod.spgemm(A, A)
+    _assert_sorted_unique(C)
+    exp = stencil3d_square_closed_form(n, C.row_ptr, C.col_idx)
+    assert not np.isnan(exp).any()
+    assert np.array_equal(C.vals, exp)
+    # every in-grid position of each of the 25 offsets is an entry
+    offs = [(a, b, c) for a in range(-2, 3) for b in range(-2, 3) for c in range(-2, 3)
+            if abs(a) + abs(b) + abs(c) <= 2]
+    assert len(offs) == 25
+    assert C.nnz == sum(max(n - abs(a), 0) * max(n - abs(b), 0) * max(n - abs(c), 0) for a, b, c in offs)
+
+
+def test_laplacian3d_squared_nnz_96():
+    offs = [(a, b, c) for a in range(-2, 3) for b in range(-2, 3) for c in range(-2, 3)
+            if abs(a) + abs(b) + abs(c) <= 2]
+    assert sum((96 - abs(a)) * (96 - abs(b)) * (96 - abs(c)) for a, b, c in offs) == 21_732_480
+
+
 # ------------------------------------------------------------- invariant
 @pytest.mark.parametrize("seed", [0, 1])
 def test_associativity_invariant(oracle_mod, seed):

@@ -79,6 +79,40 @@ def test_noalloc_transpose_long_columns_and_repeat(mods):
         assert torch.equal(v2, T.vals) and torch.equal(s2, src)
 
 
+def test_noalloc_long_column_spanning_windows(mods):
+    """A 12,000-entry column over 600,000 source rows (its transpose row
+    crosses a 262,144-key window of the long-row sort), twice in a row."""
+    nat, api = mods
+    from parity import long_column_matrix
+    dM = api.DeviceCSR.from_host(long_column_matrix())
+    T, src = _reference(nat, api, dM)
+    for _ in range(2):
+        rp2, ci2, v2, s2 = _noalloc(nat, api, dM)
+        assert torch.equal(rp2, T.row_ptr) and torch.equal(ci2, T.col_idx)
+        assert torch.equal(v2, T.vals) and torch.equal(s2, src)
+
+
+def test_noalloc_size_rule_with_and_without_t_src(mods):
+    """An input whose scratch fits with t_src given (8 bytes per entry) but
+    not without it (12 bytes per entry) runs in the first case and is
+    refused in the second."""
+    nat, api = mods
+    M = gen.random_csr(9000, 1000, 0.1, 7)
+    limit = 8 << 20
+    assert 8 * M.nnz + 4 * M.ncols + 4096 < limit < 12 * M.nnz
+    dM = api.DeviceCSR.from_host(M)
+    T, src = _reference(nat, api, dM)
+    rp2, ci2, v2, s2 = _noalloc(nat, api, dM)
+    assert torch.equal(rp2, T.row_ptr) and torch.equal(ci2, T.col_idx)
+    assert torch.equal(v2, T.vals) and torch.equal(s2, src)
+    t_rp = torch.empty(M.ncols + 1, dtype=torch.int32, device=dM.row_ptr.device)
+    t_ci = torch.empty(M.nnz, dtype=torch.int32, device=dM.row_ptr.device)
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_transpose_noalloc(dM.c_struct(), nat.SPGEMM_F64, t_rp.data_ptr(), t_ci.data_ptr(), 0, 0,
+                                     int(torch.cuda.current_stream().cuda_stream))
+    assert ei.value.status == 5
+
+
 def test_noalloc_rejects_inputs_beyond_the_fixed_scratch(mods):
     nat, api = mods
     M = gen.random_csr(200, 2_500_000, 0.002, 4)   # ~1M entries: scratch > 8 MiB without t_src
