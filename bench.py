@@ -187,9 +187,45 @@ def cpu_oracle_leg(A, B, prod, target_seconds=12.0):
     t0 = time.perf_counter()
     oracle.spgemm(sub, B)
     dt = time.perf_counter() - t0
-    return {"value": 2.0 * p / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
-            "sample": "rows i = 0 mod %d of A (%d rows, %d products, %.1f s single-threaded)"
-                      % (stride, len(rows), p, dt)}
+    out = {"value": 2.0 * p / dt / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+           "sample": "rows i = 0 mod %d of A (%d rows, %d products, %.1f s single-threaded)"
+                     % (stride, len(rows), p, dt),
+           "host_cores": os.cpu_count()}
+    out["all_cores"] = cpu_oracle_all_cores(A, B, prod, rows)
+    return out
+
+
+def _oracle_rows_task(task):
+    """Worker of cpu_oracle_all_cores: the oracle on one block of the sample
+    rows, timed in the worker (inputs already in the worker's memory)."""
+    A, B, rows = task
+    import oracle
+    oracle.build()
+    sub = oracle.select_rows(A, rows)
+    t0 = time.perf_counter()
+    oracle.spgemm(sub, B)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_all_cores(A, B, prod, rows):
+    """The same row sample on every host core: the unchanged single-threaded
+    oracle run by one spawned process per core (spawn: this process holds a
+    CUDA context) on product-balanced blocks of the sample rows.  The time is
+    the slowest worker's compute time; starting the workers and sending them
+    the inputs are not counted."""
+    import multiprocessing as mp
+    procs = max(1, os.cpu_count() or 1)
+    p = prod[rows]
+    cs = np.cumsum(p)
+    cuts = np.searchsorted(cs, cs[-1] * np.arange(1, procs) / procs) if len(cs) else []
+    blocks = [b for b in np.split(rows, cuts) if len(b)]
+    with mp.get_context("spawn").Pool(len(blocks)) as pool:
+        pool.map(_oracle_rows_task, [(A, B, b[:1]) for b in blocks])  # load the oracle in every worker
+        times = pool.map(_oracle_rows_task, [(A, B, b) for b in blocks], chunksize=1)
+    dt = max(times)
+    return {"value": 2.0 * int(p.sum()) / dt / 1e9, "unit": "GFLOP/s", "cores": len(blocks), "kind": "oracle",
+            "sample": "the same rows in %d product-balanced blocks, one spawned process per core; slowest "
+                      "worker %.2f s" % (len(blocks), dt)}
 
 
 # ------------------------------------------------------------ our step
@@ -212,6 +248,10 @@ def run_ours(args, rank, world, A, B, desc):
     kw = {} if world == 1 else {"row_range": (rb, re)}
     if args.hash_max:
         kw["hash_max"] = args.hash_max
+    if args.tune:
+        from paper_2112_10037_gb300 import autotune as at
+        kw.update(at.autotune(dA, dB))
+        desc["options"] = dict(kw)
 
     def step(profile=False):
         plan = api.Plan(dA, dB, dtype=torch.float64, **kw)
@@ -395,14 +435,14 @@ def run_e2e(args, api, torch, dev, A, B, kw, products):
     stream = torch.cuda.current_stream()
     steps = max(3, min(args.steps, 5))
 
-    def once(out=None):
+    def once(out=None, trace=None):
         d_rp = h_rp.to(dev, non_blocking=True)
         d_ci = h_ci.to(dev, non_blocking=True)
         d_v = h_v.to(dev, non_blocking=True)
         dA = api.DeviceCSR(A.nrows, A.ncols, d_rp, d_ci, d_v)
         dB = dA if B is A else api.DeviceCSR.from_host(B, device=dev)
         rp, ci, v = api.spgemm_to_host(dA, dB, dtype=torch.float64, chunks=args.e2e_chunks,
-                                       streams=args.e2e_streams, out=out, order=args.e2e_order, **kw)
+                                       streams=args.e2e_streams, out=out, order=args.e2e_order, trace=trace, **kw)
         return (rp, ci, v), ci.numel(), rp.numel()
 
     # two untimed calls: the first pins the host buffers and allocates, the
@@ -410,21 +450,32 @@ def run_e2e(args, api, torch, dev, A, B, kw, products):
     out, nnz, nrp = once()
     once(out)
     torch.cuda.synchronize()
-    ts = []
+    ts, traces = [], []
     for _ in range(steps):
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tr = {}
         ev0.record(stream)
-        once(out)
+        once(out, tr)
         ev1.record(stream)
         torch.cuda.synchronize()
         ts.append(ev0.elapsed_time(ev1))
+        traces.append(tr)
     ms = float(np.mean(ts))
     h2d = A.row_ptr.nbytes + A.col_idx.nbytes + A.vals.nbytes
     d2h = 4 * nrp + 12 * nnz
+
+    def summary(tr):
+        # host marks (ms from the call's start) and, per row range, when its
+        # numeric pass ran and when its copy to the host ran (device ms)
+        d = tr.get("device_ms", {})
+        return {"host": tr.get("host_ms", {}),
+                "numeric": [[a, b] for a, b in zip(d.get("numeric_start", []), d.get("numeric_end", []))],
+                "copy": [[a, b] for a, b in zip(d.get("copy_start", []), d.get("copy_end", []))]}
     return {"value": round(2.0 * products / (ms / 1e3) / 1e9, 2), "unit": "GFLOP/s",
             "ms_per_step": round(ms, 3), "ms_steps": [round(t, 3) for t in ts],
-            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+            "timeline": [summary(t) for t in traces]}
 
 
 # ------------------------------------------------------- reference arm
@@ -482,28 +533,53 @@ def _base_line(metric, value, unit, args, ms, desc):
 
 
 def run_batched(args):
-    """512 independent uneven products: the stacked batch (one launch per
-    pass) against one-by-one calls, full pipeline and numeric-only (graph
-    replay of the batch vs a loop of per-instance numeric calls)."""
+    """512 independent uneven products (rows log-uniform in [1024, 200000],
+    half stencil squares, half random A*B; about 9.8e9 products at full
+    size): the stacked batch -- split into waves whose stacked counts fit
+    int32, one persistent launch per pass per wave -- against one-by-one
+    calls, full pipeline and numeric only (graph replay of the batch vs a
+    loop of per-instance numeric calls).  Options from the autotuner (cached
+    per GPU and batch size class) unless --no-tune.  The phases run one after
+    the other and free their outputs, so the device holds one copy of C."""
     import torch
     from paper_2112_10037_gb300 import api, build as bld, autotune as at
     bld.build()
-    insts = list(gen.batched_instances(args.batch_count, scale_rows=args.batch_scale))
-    pairs, products = [], 0
+    insts = gen.batched_instances_parallel(args.batch_count, args.batch_scale)
+    pairs = []
     for inst in insts:
         dA = api.DeviceCSR.from_host(inst.A)
         dB = dA if inst.B is inst.A else api.DeviceCSR.from_host(inst.B)
         pairs.append((dA, dB))
-        products += int(row_products(inst.A, inst.B).sum())
+    products = int(sum(int(row_products(i.A, i.B).sum()) for i in insts))
     stream = torch.cuda.current_stream()
-    opts = {}
-    if args.tune:
-        opts = at.autotune_batch(pairs)
+    opts = {} if args.no_tune else at.autotune_batch(pairs)
+
+    def release():
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
     def batched_full():
         b = api.Batch(pairs, **opts)
         b.symbolic()
         b.numeric()
         b.close()
+    for _ in range(args.warmup):
+        batched_full()
+    t_b, _ = _events_ms(batched_full, args.steps, stream)
+    release()
+    # steady state of the batch: structure fixed, numeric passes replayed from the captured graphs
+    batch = api.Batch(pairs, **opts)
+    batch.symbolic()
+    batch.numeric()
+    batch.capture()
+    for _ in range(args.warmup):
+        batch.replay()
+    t_g, _ = _events_ms(batch.replay, args.steps, stream)
+    nnz_c, nwaves = int(batch.nnz[-1]), len(batch.waves)
+    batch.close()
+    del batch
+    release()
+
     def per_call_full():
         for dA, dB in pairs:
             pl = api.Plan(dA, dB, **opts)
@@ -511,35 +587,32 @@ def run_batched(args):
             pl.numeric(dA.vals, dB.vals)
             pl.close()
     for _ in range(args.warmup):
-        batched_full()
         per_call_full()
-    t_b, _ = _events_ms(batched_full, args.steps, stream)
     t_p, _ = _events_ms(per_call_full, args.steps, stream)
-    # steady state: structure fixed, numeric only
-    batch = api.Batch(pairs, **opts)
-    batch.symbolic()
-    batch.numeric()
-    batch.capture()
-    plans = []
-    outs = []
+    release()
+    plans, outs = [], []
     for dA, dB in pairs:
         pl = api.Plan(dA, dB, **opts)
         pl.symbolic()
         outs.append(pl.numeric(dA.vals, dB.vals))
         plans.append(pl)
+
     def loop_numeric():
         for (dA, dB), pl, (ci, v) in zip(pairs, plans, outs):
             pl.numeric(dA.vals, dB.vals, col_idx=ci, vals=v)
     for _ in range(args.warmup):
-        batch.replay()
         loop_numeric()
-    t_g, _ = _events_ms(batch.replay, args.steps, stream)
     t_l, _ = _events_ms(loop_numeric, args.steps, stream)
+    for pl in plans:
+        pl.close()
+    del plans, outs
+    release()
     gf = lambda t: 2.0 * products / (t / 1e3) / 1e9
     desc = {"workload": "batched_%d_instances_scale%g" % (len(insts), args.batch_scale),
             "instances": len(insts), "rows_total": int(sum(i.rows for i in insts)), "products": products,
-            "nnz_C": int(batch.nnz[-1]), "options": opts or "defaults",
-            "note": "rows log-uniform in [1024, 200000] x scale; half stencil squares, half random A*B"}
+            "nnz_C": nnz_c, "waves": nwaves, "options": opts or "defaults",
+            "note": "rows log-uniform in [1024, 200000] x scale; half stencil squares, half random A*B",
+            "l2": "inputs and C larger than L2"}
     out = _base_line("SpGEMM GFLOP/s (2*products/s), batched", gf(t_b), "GFLOP/s", args, t_b, desc)
     out["per_call_full_gflops"] = round(gf(t_p), 3)
     out["batched_graph_numeric_gflops"] = round(gf(t_g), 3)
@@ -807,9 +880,10 @@ def main():
                     choices=["rmat", "lap2d", "stencil3d", "batched", "galerkin", "backward", "triangles", "omar",
                              "variants"])
     ap.add_argument("--batch-count", type=int, default=512)
-    ap.add_argument("--batch-scale", type=float, default=0.1,
+    ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="row-count scale of the batched instances (1.0 = rows in [1024, 200000])")
-    ap.add_argument("--tune", action="store_true", help="autotune the options first (batched / rmat)")
+    ap.add_argument("--tune", action="store_true", help="autotune the options first (rmat)")
+    ap.add_argument("--no-tune", action="store_true", help="batched: library default options, no autotuner")
     ap.add_argument("--rmat-scale", type=int, default=18, help="R-MAT scale (18 is the benchmark workload)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--e2e-chunks", type=int, default=4,

@@ -108,7 +108,14 @@ typedef struct spgemm_opts {
                           registers: 128, 256 or 512 (0: 128); rows of 17 or more
                           products take the hash path instead unless it is off
                           (see hash_max) */
-  int32_t reserved[2];
+  int32_t rank_min;    /* > 0: rows with more products than this (and not above
+                          num_block_min) run the numeric pass with the rank-compacted
+                          accumulator: a presence bitmap over up to 2^18 columns gives
+                          each output column its position in the row, and values
+                          accumulate in an array of the row's outputs.  0 or -1: off
+                          (the default), those rows use the warp window.  Off as well
+                          with force_path >= 0 or when heavy rows are split (split_min) */
+  int32_t reserved;
 } spgemm_opts;
 
 typedef struct spgemm_plan spgemm_plan;
@@ -202,9 +209,10 @@ spgemm_status spgemm_plan_stats(spgemm_plan* plan, spgemm_stream_t stream,
  * in ms[0..n-1], in this order: analyse, symbolic register-sort, symbolic
  * hash, symbolic warp, symbolic block, scan, numeric register-sort, numeric
  * hash, numeric warp, numeric block (SPGEMM_TIMER_COUNT entries; groups
- * the plan never ran read as 0).  Creating the events is the only resource
+ * the plan never ran read as 0), and numeric rank (the rank-compacted
+ * accumulator, opts.rank_min).  Creating the events is the only resource
  * this allocates (host-side event handles). */
-#define SPGEMM_TIMER_COUNT 10
+#define SPGEMM_TIMER_COUNT 11
 spgemm_status spgemm_plan_set_profiling(spgemm_plan* plan, int on);
 spgemm_status spgemm_plan_kernel_times(spgemm_plan* plan, float* ms, int n);
 
@@ -389,6 +397,42 @@ spgemm_status spgemm_batch_capture(spgemm_batch* batch, const int32_t* c_row_ptr
 spgemm_status spgemm_graph_instantiate(spgemm_graph_t graph, spgemm_graph_exec_t* exec);
 spgemm_status spgemm_graph_launch(spgemm_graph_exec_t exec, spgemm_stream_t stream);
 void spgemm_graph_destroy(spgemm_graph_t graph, spgemm_graph_exec_t exec);
+
+/* Waves.  One spgemm_batched call stacks its instances into one CSR, so the
+ * stacked counts above and nnz of the stacked C must each stay below 2^31.
+ * A larger batch (for example 512 instances whose products add up to about
+ * 10^10) runs as several waves, each one spgemm_batched call on a run of
+ * consecutive instances with its own C.  The number of scalar products of
+ * C_i = A_i * B_i (Sec. 2.2: each nonzero A_i(r,k) scales the nnz(B_i(k,:))
+ * entries of row k of B_i) bounds nnz(C_i) from above, so waves are cut by
+ * product counts. */
+
+/* Device workspace bytes of spgemm_batch_products for n instances (host only). */
+spgemm_status spgemm_batch_products_workspace_size(int32_t n, size_t* bytes);
+
+/* products[i] (device, n int64 entries, overwritten) = the number of scalar
+ * products of C_i = A_i * B_i, i.e. the sum over the nonzeros A_i(r,k) of
+ * nnz(B_i(k,:)).  Reads only the structure of A_i and B_i (device CSR).  One
+ * launch over all instances on `stream`; does not block (the descriptors are
+ * staged from host memory before it returns).  workspace: device, at least
+ * spgemm_batch_products_workspace_size bytes, 16-byte aligned, in use until
+ * the launch has run.  SPGEMM_ERR_DIM_MISMATCH if A_i.ncols != B_i.nrows. */
+spgemm_status spgemm_batch_products(int32_t n, const spgemm_csr* As, const spgemm_csr* Bs, int64_t* products,
+                                    void* workspace, size_t workspace_bytes, spgemm_stream_t stream);
+
+/* Splits n instances into waves of consecutive instances: wave w holds
+ * instances [wave_first[w], wave_first[w+1]), *nwaves waves in all
+ * (wave_first: host, n+1 entries).  A wave takes instances in order while
+ * its stacked rows, columns, nnz(A) and nnz(B) stay below 2^31 - 1 and the
+ * sum of its products (host array, from spgemm_batch_products) stays at or
+ * below max_products (<= 0: 2^31 - 1, which keeps every wave's nnz(C) inside
+ * int32).  An instance whose products alone exceed the bound forms a wave of
+ * its own (its nnz(C) may still fit; spgemm_batch_symbolic reports
+ * SPGEMM_ERR_INDEX_OVERFLOW if not).  Host only; reads only the sizes of the
+ * descriptors.  SPGEMM_ERR_INDEX_OVERFLOW if one instance alone breaks a
+ * count limit. */
+spgemm_status spgemm_batch_waves(int32_t n, const spgemm_csr* As, const spgemm_csr* Bs, const int64_t* products,
+                                 int64_t max_products, int32_t* wave_first, int32_t* nwaves);
 
 /* The plan of the stacked product (statistics, timers, error word). */
 spgemm_plan* spgemm_batch_plan(spgemm_batch* batch);

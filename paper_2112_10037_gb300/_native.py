@@ -45,7 +45,7 @@ class spgemm_opts(ctypes.Structure):
                 ("window_block", ctypes.c_int32), ("split_min", ctypes.c_int32),
                 ("backward", ctypes.c_int32), ("num_block_min", ctypes.c_int32),
                 ("block_warps", ctypes.c_int32), ("sort_max", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("rank_min", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -96,6 +96,12 @@ _SIG = {
     "spgemm_graph_instantiate": ([_P, ctypes.POINTER(_P)], ctypes.c_int),
     "spgemm_graph_launch": ([_P, _P], ctypes.c_int),
     "spgemm_graph_destroy": ([_P, _P], None),
+    "spgemm_batch_products_workspace_size": ([ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "spgemm_batch_products": ([ctypes.c_int32, ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr), _P, _P,
+                               ctypes.c_size_t, _P], ctypes.c_int),
+    "spgemm_batch_waves": ([ctypes.c_int32, ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr), _I64P,
+                            ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+                           ctypes.c_int),
     "spgemm_batch_plan": ([_P], _P),
     "spgemm_batch_destroy": ([_P], None),
 }
@@ -200,9 +206,9 @@ def spgemm_plan_check(plan: int, stream: int) -> None:
     _check(lib().spgemm_plan_check(_P(plan), _P(stream)), "spgemm_plan_check")
 
 
-SPGEMM_TIMER_COUNT = 10
+SPGEMM_TIMER_COUNT = 11
 TIMER_NAMES = ["analyse", "sym_tiny", "sym_hash", "sym_warp", "sym_block", "scan",
-               "num_tiny", "num_hash", "num_warp", "num_block"]
+               "num_tiny", "num_hash", "num_warp", "num_block", "num_rank"]
 
 
 def spgemm_plan_set_profiling(plan: int, on: bool) -> None:
@@ -304,6 +310,31 @@ def spgemm_graph_launch(exec_: int, stream: int) -> None:
 
 def spgemm_graph_destroy(graph: int, exec_: int) -> None:
     lib().spgemm_graph_destroy(_P(graph), _P(exec_))
+
+
+def spgemm_batch_products_workspace_size(n: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(lib().spgemm_batch_products_workspace_size(n, ctypes.byref(out)), "spgemm_batch_products_workspace_size")
+    return out.value
+
+
+def spgemm_batch_products(As, Bs, products: int, workspace: int, workspace_bytes: int, stream: int) -> None:
+    n = len(As)
+    arrA, arrB = (spgemm_csr * max(n, 1))(*As), (spgemm_csr * max(n, 1))(*Bs)
+    _check(lib().spgemm_batch_products(n, arrA, arrB, _P(products), _P(workspace), ctypes.c_size_t(workspace_bytes),
+                                       _P(stream)), "spgemm_batch_products")
+
+
+def spgemm_batch_waves(As, Bs, products, max_products: int = 0):
+    """Wave boundaries [wave_first[w], wave_first[w+1]) of the instances."""
+    n = len(As)
+    arrA, arrB = (spgemm_csr * max(n, 1))(*As), (spgemm_csr * max(n, 1))(*Bs)
+    prod = (ctypes.c_int64 * max(n, 1))(*[int(p) for p in products])
+    first = (ctypes.c_int32 * (n + 1))()
+    nw = ctypes.c_int32(0)
+    _check(lib().spgemm_batch_waves(n, arrA, arrB, prod, ctypes.c_int64(max_products), first, ctypes.byref(nw)),
+           "spgemm_batch_waves")
+    return list(first)[:nw.value + 1]
 
 
 def spgemm_batch_plan(batch: int) -> int:

@@ -7,6 +7,7 @@ from __future__ import annotations
 
 import dataclasses
 import threading
+import time
 from typing import Optional
 
 import numpy as np
@@ -15,6 +16,7 @@ import torch
 from . import _native as nat
 
 _DT = {torch.float64: nat.SPGEMM_F64, torch.float32: nat.SPGEMM_F32}
+_DT_INV = {v: k for k, v in _DT.items()}
 
 
 @dataclasses.dataclass
@@ -64,7 +66,7 @@ def _stream_handle(stream=None) -> int:
 
 def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1, warp_max=0,
               window_warp=0, window_block=0, split_min=0, backward=False, num_block_min=0,
-              block_warps=0, sort_max=0, hash_max=0) -> nat.spgemm_opts:
+              block_warps=0, sort_max=0, hash_max=0, rank_min=0) -> nat.spgemm_opts:
     o = nat.spgemm_opts_default()
     o.dtype = _DT[dtype]
     o.validate = 1 if validate else 0
@@ -80,6 +82,7 @@ def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1
     o.block_warps = int(block_warps)
     o.sort_max = int(sort_max)
     o.hash_max = int(hash_max)
+    o.rank_min = int(rank_min)
     return o
 
 
@@ -238,15 +241,41 @@ def _stream_pool(dev, name, n):
 
 
 def spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int = 4, streams: int = 1, out=None,
-                   order: str = "rows", **opt_kw):
+                   order: str = "rows", trace=None, **opt_kw):
     """See _spgemm_to_host; calls on one process are serialised, since they
     share the device staging buffers (``release_staging`` frees them)."""
     with _staging_lock:
-        return _spgemm_to_host(A, B, dtype, chunks, streams, out, order, **opt_kw)
+        return _spgemm_to_host(A, B, dtype, chunks, streams, out, order, trace, **opt_kw)
+
+
+class _Trace:
+    """Timeline of one spgemm_to_host call: host clock marks and CUDA events
+    on the streams that did the work, read after the call's final sync."""
+
+    def __init__(self, comp):
+        self.t0 = time.perf_counter()
+        self.start = torch.cuda.Event(enable_timing=True)
+        self.start.record(comp)
+        self.host = {}
+        self.events = []  # (name, index, event)
+
+    def mark(self, name):
+        self.host[name] = round(1e3 * (time.perf_counter() - self.t0), 3)
+
+    def event(self, name, idx, stream):
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        self.events.append((name, idx, e))
+
+    def result(self):
+        dev = {}
+        for name, idx, e in self.events:
+            dev.setdefault(name, {})[idx] = round(self.start.elapsed_time(e), 3)
+        return {"host_ms": self.host, "device_ms": {k: [v[i] for i in sorted(v)] for k, v in dev.items()}}
 
 
 def _spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int = 4, streams: int = 1, out=None,
-                    order: str = "rows", **opt_kw):
+                    order: str = "rows", trace=None, **opt_kw):
     """C = A*B with C delivered in pinned host memory.
 
     One plan over all rows analyses the product and sizes C (one symbolic
@@ -261,14 +290,19 @@ def _spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int
     lightest last and the others heaviest first (``"rows"``: row order).
     ``out`` = (row_ptr, col_idx, vals) pinned CPU tensors to fill, reused when
     large enough.  Returns CPU tensors (row_ptr, col_idx, vals); blocks until
-    they are complete."""
+    they are complete.  ``trace``: a dict that receives the call's timeline
+    (host milliseconds at each phase; per range, the device milliseconds at
+    which its numeric pass and its copy started and ended)."""
     dev = A.row_ptr.device
     comp = torch.cuda.current_stream(dev)
     copy = _stream_pool(dev, "copy", 1)[0]
     work = _stream_pool(dev, "compute", max(1, int(streams)))
+    tr = _Trace(comp) if trace is not None else None
     m = A.nrows
     base = Plan(A, B, dtype=dtype, **opt_kw)
     rp, total = base.symbolic()
+    if tr:
+        tr.mark("symbolic")
     if total >= 2**31:
         raise nat.SpgemmError("nnz(C) does not fit int32")
     if out is None or out[0].numel() < m + 1 or out[1].numel() < total or out[2].numel() < total:
@@ -285,6 +319,8 @@ def _spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int
         cuts = []
     bounds = sorted(set([0, m] + [min(max(int(c), 0), m) for c in cuts]))
     offs = rp[torch.tensor(bounds, device=dev)].cpu().tolist()
+    if tr:
+        tr.mark("ranges")
     ranges = [(bounds[i], bounds[i + 1], offs[i], offs[i + 1] - offs[i]) for i in range(len(bounds) - 1)
               if bounds[i + 1] > bounds[i]]
     # device staging for C, kept between calls (repeated products of one
@@ -319,18 +355,30 @@ def _spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int
         seq = [by[0]] + sorted(by[2:], key=lambda i: -prods[i]) + [by[1]]
     else:
         seq = list(range(len(plans)))
+    if tr:
+        tr.mark("plans")
     for idx in seq:
         pl, (rb, re, o, n) = plans[idx], ranges[idx]
         ws = work[idx % len(work)]
+        if tr:
+            tr.event("numeric_start", idx, ws)
         with torch.cuda.stream(ws):
             pl.numeric(a_vals, b_vals, col_idx=ci, vals=v)
         done = torch.cuda.Event()
         done.record(ws)
+        if tr:
+            tr.event("numeric_end", idx, ws)
         copy.wait_event(done)
+        if tr:
+            tr.event("copy_start", idx, copy)
         if n:
             with torch.cuda.stream(copy):
                 h_ci[o:o + n].copy_(ci[o:o + n], non_blocking=True)
                 h_v[o:o + n].copy_(v[o:o + n], non_blocking=True)
+        if tr:
+            tr.event("copy_end", idx, copy)
+    if tr:
+        tr.mark("issued")
     rp.record_stream(copy)
     copy.synchronize()
     for s in work:  # the staging buffers are reused by the next call
@@ -338,6 +386,9 @@ def _spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int
     for pl in plans:
         pl.close()
     base.close()
+    if tr:
+        tr.mark("done")
+        trace.update(tr.result())
     return h_rp[:m + 1], h_ci[:total], h_v[:total]
 
 
@@ -475,34 +526,23 @@ class SpGEMMFn(torch.autograd.Function):
         return da, db, None
 
 
-class Batch:
-    """Independent products C_i = A_i * B_i computed together
-    (``spgemm_batched``): one analysis and one persistent launch per pass
-    over all instances' rows.
+class _Wave:
+    """One ``spgemm_batched`` call: a run of consecutive instances stacked
+    into one block-diagonal product with its own C."""
 
-    ``symbolic()`` sizes every C_i; ``numeric()`` fills the stacked C from
-    the current values of every A_i / B_i (update ``A_i.vals`` in place for
-    new values); ``results()`` returns per-instance DeviceCSR views.
-    ``capture()`` records the numeric pass in a CUDA graph; ``replay()``
-    launches it.
-    """
-
-    def __init__(self, pairs, dtype=torch.float64, stream=None, **opt_kw):
-        self.pairs = list(pairs)
-        self.dtype = dtype
-        self.opts = make_opts(dtype=dtype, **opt_kw)
-        self._as = [a.c_struct() for a, _ in self.pairs]
-        self._bs = [b.c_struct() for _, b in self.pairs]
-        for s_, (a, b) in zip(self._as, self.pairs):
+    def __init__(self, pairs, opts, dev, stream):
+        self.pairs = pairs
+        self.dtype = _DT_INV[opts.dtype]
+        self._as = [a.c_struct() for a, _ in pairs]
+        self._bs = [b.c_struct() for _, b in pairs]
+        for s_, (a, b) in zip(self._as, pairs):
             s_.vals = a.vals.data_ptr() if a.nnz else 0
-        for s_, (a, b) in zip(self._bs, self.pairs):
+        for s_, (a, b) in zip(self._bs, pairs):
             s_.vals = b.vals.data_ptr() if b.nnz else 0
-        dev = self.pairs[0][0].row_ptr.device if self.pairs else torch.device("cuda")
-        nbytes = nat.spgemm_batch_workspace_size(self._as, self._bs, self.opts)
+        nbytes = nat.spgemm_batch_workspace_size(self._as, self._bs, opts)
         self.workspace = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=dev)
-        self.stream = _stream_handle(stream)
-        self.handle = nat.spgemm_batched(self._as, self._bs, self.opts, self.workspace.data_ptr(), nbytes,
-                                         self.stream)
+        self.stream = stream
+        self.handle = nat.spgemm_batched(self._as, self._bs, opts, self.workspace.data_ptr(), nbytes, stream)
         self.rows = nat.spgemm_batch_rows(self.handle)
         self.device = dev
         self.row_ptr = self.col_idx = self.vals = None
@@ -518,29 +558,18 @@ class Batch:
         return self.nnz
 
     def numeric(self):
-        if self.row_ptr is None:
-            self.symbolic()
         nat.spgemm_batch_numeric(self.handle, self.row_ptr.data_ptr(),
                                  self.col_idx.data_ptr() if self.nnz[-1] else 0,
                                  self.vals.data_ptr() if self.nnz[-1] else 0, self.stream)
 
-    def capture(self):
-        """Record numeric() in a CUDA graph through ``spgemm_batch_capture``
-        (after symbolic()); ``replay()`` launches it on the current stream."""
-        if self.row_ptr is None:
-            self.symbolic()
-        self._drop_graph()
-        s = torch.cuda.Stream(device=self.device)
+    def capture(self, stream):
+        self.drop_graph()
         g = nat.spgemm_batch_capture(self.handle, self.row_ptr.data_ptr(),
                                      self.col_idx.data_ptr() if self.nnz[-1] else 0,
-                                     self.vals.data_ptr() if self.nnz[-1] else 0, int(s.cuda_stream))
+                                     self.vals.data_ptr() if self.nnz[-1] else 0, int(stream.cuda_stream))
         self.graph = (g, nat.spgemm_graph_instantiate(g))
-        return self.graph
 
-    def replay(self, stream=None):
-        nat.spgemm_graph_launch(self.graph[1], _stream_handle(stream))
-
-    def _drop_graph(self):
+    def drop_graph(self):
         if getattr(self, "graph", None):
             nat.spgemm_graph_destroy(*self.graph)
             self.graph = None
@@ -554,14 +583,103 @@ class Batch:
             e0 += n
         return out
 
-    def plan_handle(self):
-        return nat.spgemm_batch_plan(self.handle)
-
     def close(self):
-        self._drop_graph()
+        self.drop_graph()
         if getattr(self, "handle", None):
             nat.spgemm_batch_destroy(self.handle)
             self.handle = None
+
+
+class Batch:
+    """Independent products C_i = A_i * B_i computed together
+    (``spgemm_batched``): one analysis and one persistent launch per pass
+    over all instances' rows.
+
+    One stacked product must keep its counts (rows, nnz of A, B and C) inside
+    int32, so the instances are cut into waves of consecutive instances
+    (``spgemm_batch_products`` counts each instance's scalar products on the
+    device, an upper bound of its nnz(C); ``spgemm_batch_waves`` cuts the list
+    so that no wave holds more than ``max_products`` of them, 2^31 - 1 by
+    default).  Each wave is one ``spgemm_batched`` call with its own stacked
+    C; a batch that fits one wave is a single call.
+
+    ``symbolic()`` sizes every C_i; ``numeric()`` fills the stacked C of every
+    wave from the current values of every A_i / B_i (update ``A_i.vals`` in
+    place for new values); ``results()`` returns per-instance DeviceCSR views.
+    ``capture()`` records each wave's numeric pass in a CUDA graph
+    (``spgemm_batch_capture``); ``replay()`` launches them in order.
+    """
+
+    def __init__(self, pairs, dtype=torch.float64, stream=None, max_products: int = 0, **opt_kw):
+        self.pairs = list(pairs)
+        self.dtype = dtype
+        self.opts = make_opts(dtype=dtype, **opt_kw)
+        dev = self.pairs[0][0].row_ptr.device if self.pairs else torch.device("cuda")
+        self.device = dev
+        self.stream = _stream_handle(stream)
+        As = [a.c_struct() for a, _ in self.pairs]
+        Bs = [b.c_struct() for _, b in self.pairs]
+        n = len(self.pairs)
+        self.products = [0] * n
+        if n:
+            wsb = nat.spgemm_batch_products_workspace_size(n)
+            ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device=dev)
+            prod = torch.empty(n, dtype=torch.int64, device=dev)
+            nat.spgemm_batch_products(As, Bs, prod.data_ptr(), ws.data_ptr(), wsb, self.stream)
+            host = torch.empty(n, dtype=torch.int64, pin_memory=True)
+            host.copy_(prod, non_blocking=True)
+            (stream if stream is not None else torch.cuda.current_stream(dev)).synchronize()
+            self.products = [int(x) for x in host.tolist()]
+        self.wave_first = nat.spgemm_batch_waves(As, Bs, self.products, int(max_products))
+        self.waves = [_Wave(self.pairs[a:b], self.opts, dev, self.stream)
+                      for a, b in zip(self.wave_first[:-1], self.wave_first[1:])]
+        self.rows = sum(w.rows for w in self.waves)
+        self.nnz = None
+
+    def symbolic(self):
+        nnz = []
+        for w in self.waves:
+            nnz.extend(w.symbolic()[:-1])
+        self.nnz = nnz + [sum(nnz)]
+        return self.nnz
+
+    def numeric(self):
+        if self.nnz is None:
+            self.symbolic()
+        for w in self.waves:
+            w.numeric()
+
+    def capture(self):
+        """Record each wave's numeric pass in a CUDA graph through
+        ``spgemm_batch_capture`` (after symbolic()); ``replay()`` launches
+        them on the current stream."""
+        if self.nnz is None:
+            self.symbolic()
+        s = torch.cuda.Stream(device=self.device)
+        for w in self.waves:
+            w.capture(s)
+        return [w.graph for w in self.waves]
+
+    def replay(self, stream=None):
+        h = _stream_handle(stream)
+        for w in self.waves:
+            nat.spgemm_graph_launch(w.graph[1], h)
+
+    def results(self):
+        out = []
+        for w in self.waves:
+            out.extend(w.results())
+        return out
+
+    def plan_handles(self):
+        return [nat.spgemm_batch_plan(w.handle) for w in self.waves]
+
+    def plan_handle(self):
+        return self.plan_handles()[0]
+
+    def close(self):
+        for w in getattr(self, "waves", []):
+            w.close()
 
     def __del__(self):
         try:

@@ -139,6 +139,16 @@ int numeric_block_bin(const spgemm_opts& o) {
   return b < small_hi_bin(o) + 1 ? small_hi_bin(o) + 1 : b;
 }
 
+// First bin of rows whose numeric pass uses the rank-compacted block
+// accumulator: rows of more than opts.rank_min products below the block
+// window's bins; NBINS when off (rank_min <= 0, the default).
+int numeric_rank_bin(const spgemm_opts& o) {
+  if (o.force_path >= 0 || o.rank_min <= 0) return sg::NBINS;
+  const long long m = o.rank_min;
+  const int b = sg::bin_of(m) + 1;
+  return b < small_hi_bin(o) + 1 ? small_hi_bin(o) + 1 : b;
+}
+
 int numeric_window(const spgemm_opts& o) {
   return (o.window_warp == 2048 || o.window_warp == 4096) ? o.window_warp : 1024;
 }
@@ -229,6 +239,7 @@ void choose_paths(const spgemm_opts& o, sg::PathBins* pb, sg::Tuning* tu) {
   const int HASH_HI = hash_hi_bin(o);
   tu->hash_max = HASH_HI > 0 ? 1 << (HASH_HI - 1) : 0;
   tu->num_lo_block = numeric_block_bin(o);
+  tu->num_lo_rank = numeric_rank_bin(o);
   const int TINY_HI = tiny_hi_bin(o);  // register sort up to opts.sort_max products
   const int SMALL_HI = small_hi_bin(o);
   const int wb = sg::bin_of(tu->warp_max) < SMALL_HI + 1 ? SMALL_HI + 1 : sg::bin_of(tu->warp_max);
@@ -404,6 +415,9 @@ void spgemm_opts_default(spgemm_opts* o) {
   o->backward = 0;
   o->num_block_min = 0;
   o->block_warps = 0;
+  o->sort_max = 0;
+  o->rank_min = 0;
+  o->reserved = 0;
 }
 
 const char* spgemm_status_string(spgemm_status s) {
@@ -908,6 +922,76 @@ spgemm_status spgemm_graph_launch(spgemm_graph_exec_t exec, spgemm_stream_t stre
 void spgemm_graph_destroy(spgemm_graph_t graph, spgemm_graph_exec_t exec) {
   if (exec) cudaGraphExecDestroy((cudaGraphExec_t)exec);
   if (graph) cudaGraphDestroy((cudaGraph_t)graph);
+}
+
+spgemm_status spgemm_batch_products_workspace_size(int32_t n, size_t* bytes) {
+  if (!bytes || n < 0) return SPGEMM_ERR_INVALID_ARG;
+  *bytes = align_up(sizeof(sg::BatchDesc) * (size_t)(n > 0 ? n : 1));
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_batch_products(int32_t n, const spgemm_csr* As, const spgemm_csr* Bs, int64_t* products,
+                                    void* workspace, size_t workspace_bytes, spgemm_stream_t stream) {
+  if (n < 0 || (n > 0 && (!As || !Bs || !products))) return SPGEMM_ERR_INVALID_ARG;
+  if (n == 0) return SPGEMM_OK;
+  size_t need = 0;
+  spgemm_batch_products_workspace_size(n, &need);
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace) % 16) return SPGEMM_ERR_WORKSPACE;
+  std::vector<sg::BatchDesc> desc((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    spgemm_status s;
+    if ((s = check_csr(&As[i])) != SPGEMM_OK) return s;
+    if ((s = check_csr(&Bs[i])) != SPGEMM_OK) return s;
+    if (As[i].ncols != Bs[i].nrows) return SPGEMM_ERR_DIM_MISMATCH;
+    sg::BatchDesc& D = desc[(size_t)i];
+    D = sg::BatchDesc{};
+    D.a_rp = As[i].row_ptr; D.a_ci = As[i].col_idx; D.b_rp = Bs[i].row_ptr; D.b_ci = Bs[i].col_idx;
+    D.m = As[i].nrows; D.k = As[i].ncols; D.n = Bs[i].ncols; D.a_nnz = As[i].nnz; D.b_nnz = Bs[i].nnz;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SPGEMM_ERR_CUDA;
+  sg::LaunchCtx c{};
+  c.stream = (cudaStream_t)stream;
+  c.nsm = sm_count_for(dev);
+  // pageable source: the call returns once the descriptors are staged
+  if (cudaMemcpyAsync(workspace, desc.data(), sizeof(sg::BatchDesc) * (size_t)n, cudaMemcpyHostToDevice,
+                      c.stream) != cudaSuccess)
+    return SPGEMM_ERR_CUDA;
+  if (sg::launch_batch_products(c, n, (const sg::BatchDesc*)workspace, (long long*)products) != cudaSuccess)
+    return SPGEMM_ERR_CUDA;
+  return SPGEMM_OK;
+}
+
+spgemm_status spgemm_batch_waves(int32_t n, const spgemm_csr* As, const spgemm_csr* Bs, const int64_t* products,
+                                 int64_t max_products, int32_t* wave_first, int32_t* nwaves) {
+  if (n < 0 || !wave_first || !nwaves || (n > 0 && (!As || !Bs || !products))) return SPGEMM_ERR_INVALID_ARG;
+  const long long lim = (1ll << 31) - 1;  // stacked counts must stay below this (int32 indices)
+  const long long pmax = (max_products > 0 && max_products < lim) ? max_products : lim;
+  long long rows = 0, ks = 0, ncols = 0, an = 0, bn = 0, pr = 0;
+  int w = 0, count = 0;  // waves so far, instances in the open wave
+  wave_first[0] = 0;
+  for (int i = 0; i < n; ++i) {
+    spgemm_status s;
+    if ((s = check_csr(&As[i])) != SPGEMM_OK) return s;
+    if ((s = check_csr(&Bs[i])) != SPGEMM_OK) return s;
+    if (As[i].ncols != Bs[i].nrows) return SPGEMM_ERR_DIM_MISMATCH;
+    if (products[i] < 0) return SPGEMM_ERR_INVALID_ARG;
+    const bool fits = rows + As[i].nrows < lim && ks + As[i].ncols < lim && ncols + Bs[i].ncols < lim &&
+                      an + As[i].nnz < lim && bn + Bs[i].nnz < lim && pr + products[i] <= pmax;
+    if (!fits && count > 0) {  // close the open wave
+      wave_first[++w] = i;
+      rows = ks = ncols = an = bn = pr = 0;
+      count = 0;
+    }
+    rows += As[i].nrows; ks += As[i].ncols; ncols += Bs[i].ncols; an += As[i].nnz; bn += Bs[i].nnz;
+    pr += products[i];
+    ++count;
+    if (rows >= lim || ks >= lim || ncols >= lim || an >= lim || bn >= lim) return SPGEMM_ERR_INDEX_OVERFLOW;
+  }
+  if (count > 0) ++w;
+  wave_first[w] = n;
+  *nwaves = w;
+  return SPGEMM_OK;
 }
 
 spgemm_plan* spgemm_batch_plan(spgemm_batch* b) { return b ? b->plan : nullptr; }

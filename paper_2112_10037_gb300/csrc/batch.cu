@@ -103,4 +103,38 @@ cudaError_t launch_unstack_columns(const LaunchCtx& c, int n, const BatchDesc* d
   return cudaGetLastError();
 }
 
+// Per-instance product counts: products[i] = sum over A_i's nonzeros (r,k)
+// of nnz(B_i(k,:)).  grid.y = instance; blocks along x stride over A_i's
+// nonzeros, reduce in the block and add once to products[i] (zeroed first).
+__global__ void __launch_bounds__(256) k_batch_products(const BatchDesc* __restrict__ d,
+                                                        unsigned long long* __restrict__ products) {
+  __shared__ unsigned long long s_part[8];
+  const BatchDesc D = d[blockIdx.y];
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long st = (long long)gridDim.x * blockDim.x;
+  unsigned long long sum = 0;
+  for (long long p = t0; p < D.a_nnz; p += st) {
+    const int k = D.a_ci[p];
+    sum += (unsigned long long)(D.b_rp[k + 1] - D.b_rp[k]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long tot = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += s_part[w];
+    if (tot) atomicAdd(&products[blockIdx.y], tot);
+  }
+}
+
+cudaError_t launch_batch_products(const LaunchCtx& c, int n, const BatchDesc* d, long long* products) {
+  if (n <= 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(products, 0, sizeof(long long) * (size_t)n, c.stream);
+  if (e != cudaSuccess) return e;
+  k_batch_products<<<batch_grid(n, c.nsm), 256, 0, c.stream>>>(d, (unsigned long long*)products);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
 }  // namespace sg

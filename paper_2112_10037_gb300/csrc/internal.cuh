@@ -86,6 +86,7 @@ struct Tuning {
   int hash_max;        // largest P of the hash path (0: path disabled)
   int warp_max;        // largest P of the symbolic warp path
   int num_lo_block;    // numeric bins >= this use the block kernel (NBINS: never)
+  int num_lo_rank;     // numeric bins >= this (below num_lo_block) use the rank kernel (NBINS: never)
   int block_warps;     // warps per numeric block window
 };
 
@@ -244,7 +245,7 @@ struct LaunchCtx {
 // Timer groups (the order of spgemm_plan_kernel_times).
 enum Timer : int {
   T_ANALYSE = 0, T_SYM_TINY = 1, T_SYM_HASH = 2, T_SYM_WARP = 3, T_SYM_BLOCK = 4, T_SCAN = 5,
-  T_NUM_TINY = 6, T_NUM_HASH = 7, T_NUM_WARP = 8, T_NUM_BLOCK = 9, NTIMERS = 10
+  T_NUM_TINY = 6, T_NUM_HASH = 7, T_NUM_WARP = 8, T_NUM_BLOCK = 9, T_NUM_RANK = 10, NTIMERS = 11
 };
 
 inline void timer_mark(const LaunchCtx& c, int t, int end) {
@@ -312,6 +313,7 @@ cudaError_t launch_stack_values(const LaunchCtx& c, int n, int dtype, const Batc
 cudaError_t launch_unstack_columns(const LaunchCtx& c, int n, const BatchDesc* d, const int32_t* c_rp, int32_t* c_ci);
 cudaError_t launch_batch_bounds(const LaunchCtx& c, int n, const BatchDesc* d, const int32_t* c_rp, long long total_rows,
                                 int32_t* out);
+cudaError_t launch_batch_products(const LaunchCtx& c, int n, const BatchDesc* d, long long* products);
 
 // Split (heavy) rows: list positions [*hs, *hs + return value) -- the rows of
 // bins [heavy_bin, hi_bin], at most hcap of them; split row h of both passes

@@ -3,6 +3,7 @@
 
 #include "launch_util.cuh"
 #include "numblock.cuh"
+#include "numrank.cuh"
 #include "numwarp.cuh"
 #include "rowhash.cuh"
 #include "rowpass.cuh"
@@ -127,6 +128,27 @@ static cudaError_t block_num(const LaunchCtx& c, const Csr& A, const Csr& B, con
   return cudaGetLastError();
 }
 
+// Rank-compacted accumulator: 8 warps per block, 6144 value slots (two
+// blocks of 104 KB share an SM in FP64).
+constexpr int RANK_WARPS = 8;
+constexpr int RANK_CAP = 6144;
+
+template <typename T>
+static cudaError_t rank_num(const LaunchCtx& c, const Csr& A, const Csr& B, const T* av, const T* bv,
+                            const RowInfo& ri, int lo, int hi, const int32_t* c_rp, int32_t* c_ci, T* c_v) {
+  auto k = k_num_rank<RANK_WARPS, RANK_CAP, T>;
+  const size_t smem = numrank_smem_bytes<RANK_WARPS, RANK_CAP, T>();
+  const int occ = kernel_blocks_per_sm(k, RANK_WARPS * 32, smem);
+  if (occ <= 0) return cudaErrorInvalidConfiguration;
+  unsigned* counter = &c.st->work[2];
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned), c.stream);
+  if (e != cudaSuccess) return e;
+  k<<<c.nsm * occ, RANK_WARPS * 32, smem, c.stream>>>(A, B, av, bv, ri, c.st, lo, hi, c_rp, c_ci, c_v, counter,
+                                                      c.err);
+  count_launch(c);
+  return cudaGetLastError();
+}
+
 template <typename F8, typename F16, typename F32, typename F64, typename F128, typename F256, typename F512>
 static cudaError_t tiny_dispatch(const int* hist, int lo, int hi, F8 f8, F16 f16, F32 f32, F64 f64, F128 f128,
                                  F256 f256, F512 f512) {
@@ -203,6 +225,19 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
     if (e) return e;
   }
   if (hi >= blo) hi = blo - 1;
+  // rows of the rank bins (below the block window) take the rank-compacted
+  // accumulator, unless heavy rows are split (the warp kernel owns those)
+  const bool split = sp.heavy_bin < NBINS && sp.hcap > 0;
+  const int rlo = tu.num_lo_rank > lo ? tu.num_lo_rank : lo;
+  if (!split && hi >= rlo) {
+    if (!empty_bins(hist, rlo, hi)) {
+      timer_mark(c, T_NUM_RANK, 0);
+      e = rank_num<T>(c, A, B, av, bv, ri, rlo, hi, c_rp, c_ci, c_v);
+      timer_mark(c, T_NUM_RANK, 1);
+      if (e) return e;
+    }
+    hi = rlo - 1;
+  }
   if (hi >= lo && !empty_bins(hist, lo, hi)) {
     timer_mark(c, T_NUM_WARP, 0);
     switch (tu.window_warp) {

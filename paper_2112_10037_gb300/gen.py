@@ -284,6 +284,31 @@ def instance_seeds(count: int, seed: int = BATCH_SEED):
     return np.random.SeedSequence(seed).spawn(count)
 
 
+def batched_instance(i: int, count: int = 512, rows_lo: int = 1024, rows_hi: int = 200_000,
+                     seed: int = BATCH_SEED, scale_rows: float = 1.0, seeds=None) -> BatchInstance:
+    """Instance ``i`` of the batch of ``count`` (see ``batched_instances``),
+    built from its own spawned seed alone, so instances can be generated
+    independently (in parallel processes) and still match the sequence."""
+    if seeds is None:
+        seeds = instance_seeds(count, seed)
+    rng = np.random.Generator(np.random.PCG64(seeds[i]))
+    r = int(round(math.exp(rng.uniform(math.log(rows_lo), math.log(rows_hi))) * scale_rows))
+    r = max(r, 1)
+    if i < count // 2:
+        if i % 2 == 0:
+            side = max(1, int(round(math.sqrt(r))))
+            A = laplacian_2d(side)
+            return BatchInstance("stencil2d", A.nrows, A, A)
+        side = max(1, int(round(r ** (1.0 / 3.0))))
+        A = laplacian_3d(side)
+        return BatchInstance("stencil3d", A.nrows, A, A)
+    hi = min(64, r)
+    lo = min(2, hi)
+    A = random_rows(r, r, rng.integers(lo, hi + 1, size=r), rng)
+    B = random_rows(r, r, rng.integers(lo, hi + 1, size=r), rng)
+    return BatchInstance("random", r, A, B)
+
+
 def batched_instances(count: int = 512, rows_lo: int = 1024, rows_hi: int = 200_000,
                       seed: int = BATCH_SEED, scale_rows: float = 1.0):
     """Yield ``count`` independent instances (lazily, one at a time).
@@ -298,21 +323,22 @@ def batched_instances(count: int = 512, rows_lo: int = 1024, rows_hi: int = 200_
     """
     seeds = instance_seeds(count, seed)
     for i in range(count):
-        rng = np.random.Generator(np.random.PCG64(seeds[i]))
-        r = int(round(math.exp(rng.uniform(math.log(rows_lo), math.log(rows_hi))) * scale_rows))
-        r = max(r, 1)
-        if i < count // 2:
-            if i % 2 == 0:
-                side = max(1, int(round(math.sqrt(r))))
-                A = laplacian_2d(side)
-                yield BatchInstance("stencil2d", A.nrows, A, A)
-            else:
-                side = max(1, int(round(r ** (1.0 / 3.0))))
-                A = laplacian_3d(side)
-                yield BatchInstance("stencil3d", A.nrows, A, A)
-        else:
-            hi = min(64, r)
-            lo = min(2, hi)
-            A = random_rows(r, r, rng.integers(lo, hi + 1, size=r), rng)
-            B = random_rows(r, r, rng.integers(lo, hi + 1, size=r), rng)
-            yield BatchInstance("random", r, A, B)
+        yield batched_instance(i, count, rows_lo, rows_hi, seed, scale_rows, seeds)
+
+
+def _instance_task(args):
+    i, count, scale_rows = args
+    return batched_instance(i, count, scale_rows=scale_rows)
+
+
+def batched_instances_parallel(count: int = 512, scale_rows: float = 1.0, processes=None):
+    """The list ``list(batched_instances(count, scale_rows=scale_rows))``,
+    generated by a pool of spawned host processes (each instance comes from
+    its own seed, so the result is the same)."""
+    import multiprocessing as mp
+    import os
+    procs = max(1, min(count, processes or os.cpu_count() or 1))
+    if procs == 1:
+        return list(batched_instances(count, scale_rows=scale_rows))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_instance_task, [(i, count, scale_rows) for i in range(count)], chunksize=1)

@@ -76,25 +76,26 @@ def _rows(prefix, r0, r1, ncols):
 
 
 def _check_range(task):
-    r0, r1, a_ncols, b_ncols, rtol, exact, positive = task
+    px, r0, r1, a_ncols, b_ncols, rtol, exact, positive = task
     import oracle
     from paper_2112_10037_gb300.gen import CSR
-    A = _rows("a_", r0, r1, a_ncols)
-    brp = _get("b_rp")
-    B = CSR(len(brp) - 1, b_ncols, brp, _get("b_ci"), np.asarray(_get("b_v"), np.float64))
+    A = _rows(px + "a_", r0, r1, a_ncols)
+    brp = _get(px + "b_rp")
+    B = CSR(len(brp) - 1, b_ncols, brp, _get(px + "b_ci"), np.asarray(_get(px + "b_v"), np.float64))
     R = oracle.spgemm(A, B)
-    crp = _get("c_rp").astype(np.int64)
+    crp = _get(px + "c_rp").astype(np.int64)
     lo, hi = int(crp[r0]), int(crp[r1])
-    out = {"r0": r0, "r1": r1, "nnz": hi - lo, "rp_ok": True, "ci_ok": True, "max_err": 0.0, "bad": 0}
+    out = {"item": px, "r0": r0, "r1": r1, "nnz": hi - lo, "rp_ok": True, "ci_ok": True, "max_err": 0.0,
+           "bad": 0}
     if not np.array_equal(crp[r0:r1 + 1] - lo, np.asarray(R.row_ptr, np.int64)):
         out["rp_ok"] = False
         return out
-    ci = _get("c_ci")[lo:hi]
+    ci = _get(px + "c_ci")[lo:hi]
     if not np.array_equal(ci, R.col_idx):
         out["ci_ok"] = False
         out["first_ci"] = int(np.flatnonzero(ci != R.col_idx)[0]) + lo
         return out
-    got = np.asarray(_get("c_v")[lo:hi], np.float64)
+    got = np.asarray(_get(px + "c_v")[lo:hi], np.float64)
     ref = np.asarray(R.vals, np.float64)
     if exact:
         bad = got != ref
@@ -124,17 +125,40 @@ def balanced_ranges(prod, nranges):
     return [(int(x), int(y)) for x, y in zip(b[:-1], b[1:]) if y > x]
 
 
+def _tasks(A, B, prod, prefix, rtol, exact, nranges):
+    positive = bool(len(A.vals) == 0 or np.min(A.vals) > 0) and bool(len(B.vals) == 0 or np.min(B.vals) > 0)
+    return [(prefix, r0, r1, A.ncols, B.ncols, rtol, exact, positive) for r0, r1 in balanced_ranges(prod, nranges)]
+
+
+def put_inputs(store, A, B, prefix=""):
+    for name, arr in (("a_rp", A.row_ptr), ("a_ci", A.col_idx), ("a_v", np.asarray(A.vals, np.float64)),
+                      ("b_rp", B.row_ptr), ("b_ci", B.col_idx), ("b_v", np.asarray(B.vals, np.float64))):
+        store.put(prefix + name, arr)
+
+
 def compare_product(A, B, store, prod, rtol=1e-12, exact=False, processes=None, ranges_per_process=6):
     """Compares the whole product with the oracle.  ``store`` holds the
     device result as "c_rp" (int64), "c_ci" and "c_v" (see ``Store``).
     Returns the list of per-range results."""
     processes = processes or os.cpu_count() or 4
-    positive = bool(len(A.vals) == 0 or np.min(A.vals) > 0) and bool(len(B.vals) == 0 or np.min(B.vals) > 0)
-    for name, arr in (("a_rp", A.row_ptr), ("a_ci", A.col_idx), ("a_v", np.asarray(A.vals, np.float64)),
-                      ("b_rp", B.row_ptr), ("b_ci", B.col_idx), ("b_v", np.asarray(B.vals, np.float64))):
-        store.put(name, arr)
-    tasks = [(r0, r1, A.ncols, B.ncols, rtol, exact, positive)
-             for r0, r1 in balanced_ranges(prod, processes * ranges_per_process)]
+    put_inputs(store, A, B)
+    tasks = _tasks(A, B, prod, "", rtol, exact, processes * ranges_per_process)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(processes, initializer=_init, initargs=(store.specs,)) as pool:
+        return pool.map(_check_range, tasks, chunksize=1)
+
+
+def compare_many(items, store, processes=None, ranges_per_item=4):
+    """Several products compared in one pool: ``items`` is a list of
+    (prefix, A, B, prod, rtol, exact) whose device results the caller put in
+    ``store`` as prefix + "c_rp" / "c_ci" / "c_v"; the inputs are stored
+    here.  Returns the per-range results of all items (each tagged with its
+    prefix as "item")."""
+    processes = processes or os.cpu_count() or 4
+    tasks = []
+    for prefix, A, B, prod, rtol, exact in items:
+        put_inputs(store, A, B, prefix)
+        tasks += _tasks(A, B, prod, prefix, rtol, exact, ranges_per_item)
     ctx = mp.get_context("spawn")
     with ctx.Pool(processes, initializer=_init, initargs=(store.specs,)) as pool:
         return pool.map(_check_range, tasks, chunksize=1)
@@ -145,12 +169,11 @@ def summarise(res):
     max_err = max((r["max_err"] for r in res), default=0.0)
     entries = sum(r["nnz"] for r in res)
     for r in res:
+        where = "%srows [%d, %d)" % (r["item"] + " " if r.get("item") else "", r["r0"], r["r1"])
         if not r["rp_ok"]:
-            return False, max_err, entries, "row sizes differ in rows [%d, %d)" % (r["r0"], r["r1"])
+            return False, max_err, entries, "row sizes differ in " + where
         if not r["ci_ok"]:
-            return False, max_err, entries, "columns differ in rows [%d, %d) at entry %d" % (
-                r["r0"], r["r1"], r["first_ci"])
+            return False, max_err, entries, "columns differ in %s at entry %d" % (where, r["first_ci"])
         if r["bad"]:
-            return False, max_err, entries, "%d values outside the bound in rows [%d, %d)" % (
-                r["bad"], r["r0"], r["r1"])
+            return False, max_err, entries, "%d values outside the bound in %s" % (r["bad"], where)
     return True, max_err, entries, "ok"

@@ -116,3 +116,51 @@ def test_graph_calls_host_checks_without_gpu(libpath):
         nat.spgemm_graph_launch(0, 0)
     assert ei.value.status == 1
     nat.spgemm_graph_destroy(0, 0)  # NULL handles: nothing to free
+
+
+def _desc(m, k, nnz):
+    s = nat.spgemm_csr()
+    s.nrows, s.ncols, s.nnz = m, k, nnz
+    s.row_ptr = 16  # sizes only: never dereferenced by the wave split
+    s.col_idx = 16 if nnz else 0
+    return s
+
+
+def test_batch_waves_host_only(libpath):
+    """spgemm_batch_waves cuts consecutive instances into waves whose
+    product sums stay within the bound and whose stacked counts fit int32;
+    an oversized instance stands alone; everything is host logic."""
+    As = [_desc(10, 10, 30) for _ in range(7)]
+    Bs = [_desc(10, 10, 30) for _ in range(7)]
+    prod = [40, 50, 30, 100, 5, 5, 90]
+    assert nat.spgemm_batch_waves(As, Bs, prod, 100) == [0, 2, 3, 4, 7]  # 5 + 5 + 90 = 100 fits
+    assert nat.spgemm_batch_waves(As, Bs, prod, 1000) == [0, 7]
+    assert nat.spgemm_batch_waves(As, Bs, prod, 0) == [0, 7]            # default bound 2^31 - 1
+    assert nat.spgemm_batch_waves(As, Bs, [250] + prod[1:], 100)[:3] == [0, 1, 3]  # 250 alone
+    assert nat.spgemm_batch_waves([], [], [], 0) == [0]
+    # the default bound keeps every wave's product sum (an upper bound of its nnz(C)) inside int32
+    big = [1 << 30, 1 << 30, 1 << 30, 5]
+    w = nat.spgemm_batch_waves(As[:4], Bs[:4], big, 0)
+    assert w == [0, 1, 2, 4]
+    for a, b in zip(w[:-1], w[1:]):
+        assert sum(big[a:b]) < (1 << 31) - 1 or b - a == 1
+    # stacked rows would reach 2^31 - 1: a new wave starts
+    huge = [_desc((1 << 30) + 5, 10, 0), _desc((1 << 30) + 5, 10, 0)]
+    assert nat.spgemm_batch_waves(huge, [_desc(10, 10, 0)] * 2, [0, 0], 0) == [0, 1, 2]
+    with pytest.raises(nat.SpgemmError) as ei:  # shapes are checked
+        nat.spgemm_batch_waves([_desc(4, 5, 0)], [_desc(6, 3, 0)], [0], 0)
+    assert ei.value.status == 2
+    with pytest.raises(nat.SpgemmError) as ei:  # negative product count
+        nat.spgemm_batch_waves(As[:1], Bs[:1], [-1], 0)
+    assert ei.value.status == 1
+
+
+def test_batch_products_host_checks_without_gpu(libpath):
+    assert nat.spgemm_batch_products_workspace_size(3) >= 3 * 8
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_batch_products([_desc(4, 5, 0)], [_desc(5, 3, 0)], 256, 0, 0, 0)
+    assert ei.value.status == 5  # workspace missing
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_batch_products([_desc(4, 5, 0)], [_desc(6, 3, 0)], 256, 256, 1 << 12, 0)
+    assert ei.value.status == 2
+    nat.spgemm_batch_products([], [], 0, 0, 0, 0)  # nothing to count

@@ -67,3 +67,28 @@ def test_compare_exact_mode(oracle_mod):
         assert not ok and "values" in msg
     finally:
         st.close()
+
+
+def test_compare_many_reports_the_item(oracle_mod):
+    """Several products in one pool: all pass as stored, and a value planted
+    wrong in the second item's copy is reported with that item's tag."""
+    items, st = [], fullcmp.Store(1 << 24)
+    try:
+        for k, (A, B) in enumerate([(gen.laplacian_2d(12), None), (gen.random_csr(60, 50, 0.1, 3),
+                                                                    gen.random_csr(50, 70, 0.1, 4))]):
+            B = A if B is None else B
+            C = oracle_mod.spgemm(A, B)
+            px = "i%d_" % k
+            st.put(px + "c_rp", np.asarray(C.row_ptr, np.int64))
+            st.put(px + "c_ci", C.col_idx)
+            st.put(px + "c_v", C.vals)
+            items.append((px, A, B, oracle_mod.row_products(A, B), 1e-12, k == 0))
+        ok, err, n, msg = fullcmp.summarise(fullcmp.compare_many(items, st, processes=2))
+        assert ok, msg
+        v = np.memmap(st.specs["i1_c_v"][0], dtype=np.float64, mode="r+", shape=st.specs["i1_c_v"][1])
+        v[5] = v[5] + 1.0
+        v.flush()
+        ok, err, n, msg = fullcmp.summarise(fullcmp.compare_many(items, st, processes=2))
+        assert not ok and "i1_" in msg and "values" in msg
+    finally:
+        st.close()
