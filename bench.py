@@ -248,10 +248,14 @@ def run_ours(args, rank, world, A, B, desc):
     kw = {} if world == 1 else {"row_range": (rb, re)}
     if args.hash_max:
         kw["hash_max"] = args.hash_max
+    for item in args.opt:
+        k, v = item.split("=", 1)
+        kw[k] = int(v)
     if args.tune:
         from paper_2112_10037_gb300 import autotune as at
         kw.update(at.autotune(dA, dB))
-        desc["options"] = dict(kw)
+    if args.opt or args.tune:
+        desc["options"] = {k: v for k, v in kw.items() if k != "row_range"}
 
     def step(profile=False):
         plan = api.Plan(dA, dB, dtype=torch.float64, **kw)
@@ -552,14 +556,20 @@ def run_batched(args):
         pairs.append((dA, dB))
     products = int(sum(int(row_products(i.A, i.B).sum()) for i in insts))
     stream = torch.cuda.current_stream()
-    opts = {} if args.no_tune else at.autotune_batch(pairs)
+    opts = {}
+    for item in args.opt:
+        k, v = item.split("=", 1)
+        opts[k] = int(v)
+    if not args.no_tune and not args.opt:
+        opts = at.autotune_batch(pairs)
+    wave_kw = {"max_b_nnz": args.batch_max_b_nnz} if args.batch_max_b_nnz else {}
 
     def release():
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
 
     def batched_full():
-        b = api.Batch(pairs, **opts)
+        b = api.Batch(pairs, **wave_kw, **opts)
         b.symbolic()
         b.numeric()
         b.close()
@@ -568,7 +578,7 @@ def run_batched(args):
     t_b, _ = _events_ms(batched_full, args.steps, stream)
     release()
     # steady state of the batch: structure fixed, numeric passes replayed from the captured graphs
-    batch = api.Batch(pairs, **opts)
+    batch = api.Batch(pairs, **wave_kw, **opts)
     batch.symbolic()
     batch.numeric()
     batch.capture()
@@ -610,7 +620,7 @@ def run_batched(args):
     gf = lambda t: 2.0 * products / (t / 1e3) / 1e9
     desc = {"workload": "batched_%d_instances_scale%g" % (len(insts), args.batch_scale),
             "instances": len(insts), "rows_total": int(sum(i.rows for i in insts)), "products": products,
-            "nnz_C": nnz_c, "waves": nwaves, "options": opts or "defaults",
+            "nnz_C": nnz_c, "waves": nwaves, "options": opts or "defaults", **wave_kw,
             "note": "rows log-uniform in [1024, 200000] x scale; half stencil squares, half random A*B",
             "l2": "inputs and C larger than L2"}
     out = _base_line("SpGEMM GFLOP/s (2*products/s), batched", gf(t_b), "GFLOP/s", args, t_b, desc)
@@ -797,6 +807,182 @@ def run_triangles(args):
     return res
 
 
+def run_stencil_device(args):
+    """C = A*A for the 3D 7-point operator on 96^3 (every row on the
+    lane-per-row hash path): whole product (analyse, symbolic, numeric) with
+    inputs resident, L2 flushed between steps; per-kernel CUDA-event times
+    and the numeric pass's HBM fraction (A, the B rows touched, C written)."""
+    import torch
+    from paper_2112_10037_gb300 import api, build as bld, _native as nat
+    bld.build()
+    A = gen.laplacian_3d(96)
+    products = int(row_products(A, A).sum())
+    dA = api.DeviceCSR.from_host(A)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(profile=False):
+        plan = api.Plan(dA, dA)
+        if profile:
+            nat.spgemm_plan_set_profiling(plan.handle, True)
+        rp, nnz = plan.symbolic()
+        plan.numeric(dA.vals, dA.vals)
+        return plan, nnz
+    for _ in range(args.warmup):
+        step()[0].close()
+    ts, ks = [], []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan, nnz = step(profile=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+        ks.append(nat.spgemm_plan_kernel_times(plan.handle))
+        plan.close()
+    ms = float(np.mean(ts))
+    kms = {n: round(float(np.mean([k[n] for k in ks])), 4) for n in ks[0] if np.mean([k[n] for k in ks]) > 0}
+    num_ms = kms.get("num_hash", 0.0) + kms.get("num_tiny", 0.0)
+    byte_model = (8 * A.nrows + 12 * A.nnz) * 2 + 8 * A.nrows + 12 * nnz  # A, B (= A, counted again), C
+    peak, _ = measured_hbm_peak()
+    return {"ms": round(ms, 4), "gflops": round(2.0 * products / (ms / 1e3) / 1e9, 2), "kernel_ms": kms,
+            "numeric_ms": round(num_ms, 4), "numeric_hbm_frac": round(byte_model / (num_ms / 1e3) / 1e9 / peak, 4)
+            if num_ms else None, "products": products, "nnz_C": int(nnz)}
+
+
+def run_sharing(args):
+    """B-row sharing and the row order (Sec. 3's buffering idea, Eq. 1's
+    OMAR): on R-MAT scale 20 (A = 193 MB, larger than the 129 MB L2, so B's
+    rows no longer all stay in L2) the same set of rows of A multiplies A in
+    two orders -- the generator's row order and rows sorted by their
+    heaviest column (the B row with the most entries they touch), so rows
+    that read the same hub rows of B run close together -- and the numeric
+    pass is timed for both.  The rows taken are the first rows whose products
+    stay below 2.5e9 (nnz(C) inside int32).  The kernels take rows by
+    descending product bin and, inside a bin, in row order, so the sort
+    changes which rows run concurrently."""
+    import torch
+    from paper_2112_10037_gb300 import api, build as bld, _native as nat
+    bld.build()
+    scale = 20
+    A = gen.rmat(scale, 16)
+    prod = row_products(A, A)
+    cs = np.cumsum(prod)
+    r1 = int(np.searchsorted(cs, 2.5e9))
+    rows = np.arange(r1)
+    lens = np.diff(A.row_ptr.astype(np.int64))
+    rp = A.row_ptr.astype(np.int64)
+    # heaviest column of each row: its nonzero whose B row is longest
+    nz_row = np.repeat(np.arange(A.nrows), lens)
+    w = lens[A.col_idx]
+    first = np.lexsort((-w, nz_row))  # by row, longest B row first
+    heavy = np.full(A.nrows, -1, np.int64)
+    starts = rp[:-1][lens > 0]
+    heavy[lens > 0] = A.col_idx[first[starts]]
+    order = np.lexsort((rows, heavy[rows]))
+
+    def take_rows(M, sel):
+        """The rows sel of M as a CSR (input slicing only)."""
+        mrp = M.row_ptr.astype(np.int64)
+        ln = mrp[sel + 1] - mrp[sel]
+        nrp = np.zeros(len(sel) + 1, np.int64)
+        np.cumsum(ln, out=nrp[1:])
+        idx = np.repeat(mrp[sel] - nrp[:-1], ln) + np.arange(int(nrp[-1]))
+        return gen.CSR(len(sel), M.ncols, nrp.astype(np.int32), M.col_idx[idx], M.vals[idx])
+    variants = {"row_order": take_rows(A, rows), "heaviest_column_order": take_rows(A, rows[order])}
+    dB = api.DeviceCSR.from_host(A)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    out = {}
+    for name, S in variants.items():
+        dS = api.DeviceCSR.from_host(S)
+        plan = api.Plan(dS, dB)
+        nat.spgemm_plan_set_profiling(plan.handle, True)
+        rp_c, nnz = plan.symbolic()
+        ci = torch.empty(nnz, dtype=torch.int32, device="cuda")
+        v = torch.empty(nnz, dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            plan.numeric(dS.vals, dB.vals, col_idx=ci, vals=v)
+        ts, ks = [], []
+        for _ in range(args.steps):
+            flush.fill_(1)
+            t, _ = _events_ms(lambda: plan.numeric(dS.vals, dB.vals, col_idx=ci, vals=v), 1, stream)
+            ts.append(t)
+            ks.append(nat.spgemm_plan_kernel_times(plan.handle))
+        p = int(prod[rows].sum())
+        out[name] = {"numeric_ms": round(float(np.mean(ts)), 3),
+                     "gflops": round(2.0 * p / (float(np.mean(ts)) / 1e3) / 1e9, 2),
+                     "num_warp_ms": round(float(np.mean([k["num_warp"] for k in ks])), 3),
+                     "num_block_ms": round(float(np.mean([k["num_block"] for k in ks])), 3),
+                     "omar_32_pct": round(api.omar(dS, 32), 2)}
+        plan.close()
+        del dS, ci, v
+        torch.cuda.empty_cache()
+    desc = {"workload": "rmat_s20_rows_0_%d_AxA" % r1, "rows": r1, "products": int(prod[rows].sum()),
+            "nnz_A_bytes": int(12 * A.nnz + 4 * (A.nrows + 1)), "l2_bytes": L2_BYTES}
+    res = _base_line("numeric GFLOP/s, rows in generator order vs sorted by heaviest column",
+                     out["heaviest_column_order"]["gflops"], "GFLOP/s", args,
+                     out["heaviest_column_order"]["numeric_ms"], desc)
+    res["orders"] = out
+    return res
+
+
+def run_secondary(args):
+    """The other workloads of the measurement plan, each in a short form, for
+    the default bench line: the 3D stencil product, the Galerkin chain replay,
+    the differentiation workload's forward and backward passes, triangle
+    counting on the R-MAT scale-18 graph and the 512-instance batched
+    workload at its stated size against one-by-one calls."""
+    import copy
+    import torch
+    a = copy.copy(args)
+    a.steps, a.warmup, a.no_cpu = max(3, min(args.steps, 5)), 2, True
+    out = {}
+
+    def keep(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as exc:  # reported in the line, the headline stands
+            out[name] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+
+    keep("stencil3d_96_AxA", lambda: run_stencil_device(a))
+
+    def gal():
+        r = run_galerkin(a)
+        return {"replay_ms": r["ms_per_step"], "gflops": r["value"], "hbm_frac": r["roofline"]["frac"],
+                "two_plain_calls_ms": r["two_plain_calls_ms"]}
+    keep("galerkin_96_graph_replay", gal)
+
+    def bwd():
+        r = run_backward(a)
+        return {"f64": r["f64"], "f32": r["f32"]}
+    keep("differentiation_65536sq", bwd)
+
+    def tri():
+        t = copy.copy(a)
+        t.rmat_scale = 18
+        r = run_triangles(t)
+        return {"ms": r["ms_per_step"], "gflops": r["value"], "triangles": r["config"]["triangles"]}
+    keep("triangles_rmat_s18", tri)
+
+    def bat():
+        b = copy.copy(a)
+        b.steps, b.warmup, b.batch_scale, b.batch_count = 1, 1, 1.0, 512
+        b.no_tune, b.opt, b.batch_max_b_nnz = True, [], 8_000_000
+        r = run_batched(b)
+        return {"batched_gflops": r["value"], "per_call_gflops": r["per_call_full_gflops"],
+                "batched_graph_numeric_gflops": r["batched_graph_numeric_gflops"],
+                "per_call_numeric_gflops": r["per_call_numeric_gflops"], "speedup_full": r["speedup_full"],
+                "speedup_numeric": r["speedup_numeric"], "waves": r["config"]["waves"],
+                "products": r["config"]["products"], "nnz_C": r["config"]["nnz_C"]}
+    keep("batched_512_full_size", bat)
+    return out
+
+
 def run_omar(args):
     """OMAR (Eq. 1) of the buffering scheme of Sec. 3 for 2..32 computing
     units on the R-MAT and 3D stencil matrices, computed on the device (one
@@ -878,14 +1064,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat",
                     choices=["rmat", "lap2d", "stencil3d", "batched", "galerkin", "backward", "triangles", "omar",
-                             "variants"])
+                             "variants", "stencil_device", "sharing"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="row-count scale of the batched instances (1.0 = rows in [1024, 200000])")
     ap.add_argument("--tune", action="store_true", help="autotune the options first (rmat)")
     ap.add_argument("--no-tune", action="store_true", help="batched: library default options, no autotuner")
+    ap.add_argument("--batch-max-b-nnz", type=int, default=0,
+                    help="batched: at most this many B entries per wave (0: waves bounded by products only)")
+    ap.add_argument("--opt", action="append", default=[], metavar="NAME=VALUE",
+                    help="plan option (spgemm_opts field) for the product, e.g. --opt rank_min=1024")
     ap.add_argument("--rmat-scale", type=int, default=18, help="R-MAT scale (18 is the benchmark workload)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="default workload: skip the short runs of the other workloads")
     ap.add_argument("--e2e-chunks", type=int, default=4,
                     help="row ranges of the end-to-end leg (computed while earlier ranges are copied back)")
     ap.add_argument("--e2e-streams", type=int, default=1, help="compute streams of the end-to-end leg")
@@ -902,10 +1094,12 @@ def main():
         A, B, desc = make_workload(args.workload, args.rmat_scale)
         print(json.dumps(run_reference(args, A, B, desc)), flush=True)
         return
-    if args.workload in ("batched", "galerkin", "backward", "triangles", "omar", "variants"):
+    if args.workload in ("batched", "galerkin", "backward", "triangles", "omar", "variants", "stencil_device",
+                         "sharing"):
         if rank == 0:
             runner = {"batched": run_batched, "galerkin": run_galerkin, "backward": run_backward,
-                      "triangles": run_triangles, "omar": run_omar, "variants": run_variants}[args.workload]
+                      "triangles": run_triangles, "omar": run_omar, "variants": run_variants,
+                      "stencil_device": run_stencil_device, "sharing": run_sharing}[args.workload]
             print(json.dumps(runner(args)), flush=True)
         return
     if world > 1:
@@ -915,6 +1109,8 @@ def main():
     A, B, desc = make_workload(args.workload, args.rmat_scale)
     out = run_ours(args, rank, world, A, B, desc)
     if rank == 0:
+        if world == 1 and args.workload == "rmat" and args.rmat_scale == 18 and not args.no_secondary:
+            out["secondary"] = run_secondary(args)
         if not args.no_cpu and world == 1:
             out["cpu_baseline"] = cpu_oracle_leg(A, B, row_products(A, B))
         print(json.dumps(out), flush=True)

@@ -115,7 +115,10 @@ typedef struct spgemm_opts {
                           accumulate in an array of the row's outputs.  0 or -1: off
                           (the default), those rows use the warp window.  Off as well
                           with force_path >= 0 or when heavy rows are split (split_min) */
-  int32_t reserved;
+  int32_t rank_accum;  /* where the rank-compacted accumulator sums its values: 0 (default)
+                          in C itself, zeroed first, by reductions in the L2 cache's atomic
+                          units; 1 in shared memory, 6144 ranks per pass over the row's
+                          products */
 } spgemm_opts;
 
 typedef struct spgemm_plan spgemm_plan;
@@ -232,7 +235,9 @@ spgemm_status spgemm_plan_check(spgemm_plan* plan, spgemm_stream_t stream);
  * of A's nonzeros; entries of rows outside the plan's row range are left
  * untouched) and db_vals (aligned with B's col_idx; sums over the plan's
  * rows only) are overwritten; either may be NULL to skip it.  Each output is
- * one sequential fused multiply-add chain, so the result is deterministic.
+ * summed in a fixed order -- one fused multiply-add chain when it has at most
+ * 128 terms, otherwise 32 lane chains added by a fixed shuffle tree -- so the
+ * result is deterministic (the same bits on every call).
  * Does not block, allocates nothing. */
 spgemm_status spgemm_backward(spgemm_plan* plan, const void* a_vals, const void* b_vals,
                               const int32_t* c_row_ptr, const int32_t* c_col_idx,
@@ -426,13 +431,15 @@ spgemm_status spgemm_batch_products(int32_t n, const spgemm_csr* As, const spgem
  * its stacked rows, columns, nnz(A) and nnz(B) stay below 2^31 - 1 and the
  * sum of its products (host array, from spgemm_batch_products) stays at or
  * below max_products (<= 0: 2^31 - 1, which keeps every wave's nnz(C) inside
- * int32).  An instance whose products alone exceed the bound forms a wave of
- * its own (its nnz(C) may still fit; spgemm_batch_symbolic reports
- * SPGEMM_ERR_INDEX_OVERFLOW if not).  Host only; reads only the sizes of the
- * descriptors.  SPGEMM_ERR_INDEX_OVERFLOW if one instance alone breaks a
- * count limit. */
+ * int32), and the sum of its nnz(B_i) at or below max_b_nnz (<= 0: no bound
+ * beyond int32; a bound sized to the L2 cache keeps each wave's B operands,
+ * which every row of the wave re-reads, resident there).  An instance that
+ * alone exceeds a bound forms a wave of its own (its nnz(C) may still fit;
+ * spgemm_batch_symbolic reports SPGEMM_ERR_INDEX_OVERFLOW if not).  Host
+ * only; reads only the sizes of the descriptors.  SPGEMM_ERR_INDEX_OVERFLOW
+ * if one instance alone breaks a count limit. */
 spgemm_status spgemm_batch_waves(int32_t n, const spgemm_csr* As, const spgemm_csr* Bs, const int64_t* products,
-                                 int64_t max_products, int32_t* wave_first, int32_t* nwaves);
+                                 int64_t max_products, int64_t max_b_nnz, int32_t* wave_first, int32_t* nwaves);
 
 /* The plan of the stacked product (statistics, timers, error word). */
 spgemm_plan* spgemm_batch_plan(spgemm_batch* batch);

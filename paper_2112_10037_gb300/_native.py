@@ -45,7 +45,7 @@ class spgemm_opts(ctypes.Structure):
                 ("window_block", ctypes.c_int32), ("split_min", ctypes.c_int32),
                 ("backward", ctypes.c_int32), ("num_block_min", ctypes.c_int32),
                 ("block_warps", ctypes.c_int32), ("sort_max", ctypes.c_int32),
-                ("rank_min", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("rank_min", ctypes.c_int32), ("rank_accum", ctypes.c_int32)]
 
 
 _lib = None
@@ -100,7 +100,8 @@ _SIG = {
     "spgemm_batch_products": ([ctypes.c_int32, ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr), _P, _P,
                                ctypes.c_size_t, _P], ctypes.c_int),
     "spgemm_batch_waves": ([ctypes.c_int32, ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr), _I64P,
-                            ctypes.c_int64, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+                            ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
+                            ctypes.POINTER(ctypes.c_int32)],
                            ctypes.c_int),
     "spgemm_batch_plan": ([_P], _P),
     "spgemm_batch_destroy": ([_P], None),
@@ -325,15 +326,15 @@ def spgemm_batch_products(As, Bs, products: int, workspace: int, workspace_bytes
                                        _P(stream)), "spgemm_batch_products")
 
 
-def spgemm_batch_waves(As, Bs, products, max_products: int = 0):
+def spgemm_batch_waves(As, Bs, products, max_products: int = 0, max_b_nnz: int = 0):
     """Wave boundaries [wave_first[w], wave_first[w+1]) of the instances."""
     n = len(As)
     arrA, arrB = (spgemm_csr * max(n, 1))(*As), (spgemm_csr * max(n, 1))(*Bs)
     prod = (ctypes.c_int64 * max(n, 1))(*[int(p) for p in products])
     first = (ctypes.c_int32 * (n + 1))()
     nw = ctypes.c_int32(0)
-    _check(lib().spgemm_batch_waves(n, arrA, arrB, prod, ctypes.c_int64(max_products), first, ctypes.byref(nw)),
-           "spgemm_batch_waves")
+    _check(lib().spgemm_batch_waves(n, arrA, arrB, prod, ctypes.c_int64(max_products), ctypes.c_int64(max_b_nnz),
+                                    first, ctypes.byref(nw)), "spgemm_batch_waves")
     return list(first)[:nw.value + 1]
 
 

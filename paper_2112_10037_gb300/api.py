@@ -66,7 +66,7 @@ def _stream_handle(stream=None) -> int:
 
 def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1, warp_max=0,
               window_warp=0, window_block=0, split_min=0, backward=False, num_block_min=0,
-              block_warps=0, sort_max=0, hash_max=0, rank_min=0) -> nat.spgemm_opts:
+              block_warps=0, sort_max=0, hash_max=0, rank_min=0, rank_accum=0) -> nat.spgemm_opts:
     o = nat.spgemm_opts_default()
     o.dtype = _DT[dtype]
     o.validate = 1 if validate else 0
@@ -83,6 +83,7 @@ def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1
     o.sort_max = int(sort_max)
     o.hash_max = int(hash_max)
     o.rank_min = int(rank_min)
+    o.rank_accum = int(rank_accum)
     return o
 
 
@@ -600,8 +601,9 @@ class Batch:
     (``spgemm_batch_products`` counts each instance's scalar products on the
     device, an upper bound of its nnz(C); ``spgemm_batch_waves`` cuts the list
     so that no wave holds more than ``max_products`` of them, 2^31 - 1 by
-    default).  Each wave is one ``spgemm_batched`` call with its own stacked
-    C; a batch that fits one wave is a single call.
+    default, and, with ``max_b_nnz``, no more B entries than that).  Each wave
+    is one ``spgemm_batched`` call with its own stacked C; a batch that fits
+    one wave is a single call.
 
     ``symbolic()`` sizes every C_i; ``numeric()`` fills the stacked C of every
     wave from the current values of every A_i / B_i (update ``A_i.vals`` in
@@ -610,7 +612,8 @@ class Batch:
     (``spgemm_batch_capture``); ``replay()`` launches them in order.
     """
 
-    def __init__(self, pairs, dtype=torch.float64, stream=None, max_products: int = 0, **opt_kw):
+    def __init__(self, pairs, dtype=torch.float64, stream=None, max_products: int = 0, max_b_nnz: int = 0,
+                 **opt_kw):
         self.pairs = list(pairs)
         self.dtype = dtype
         self.opts = make_opts(dtype=dtype, **opt_kw)
@@ -630,7 +633,7 @@ class Batch:
             host.copy_(prod, non_blocking=True)
             (stream if stream is not None else torch.cuda.current_stream(dev)).synchronize()
             self.products = [int(x) for x in host.tolist()]
-        self.wave_first = nat.spgemm_batch_waves(As, Bs, self.products, int(max_products))
+        self.wave_first = nat.spgemm_batch_waves(As, Bs, self.products, int(max_products), int(max_b_nnz))
         self.waves = [_Wave(self.pairs[a:b], self.opts, dev, self.stream)
                       for a, b in zip(self.wave_first[:-1], self.wave_first[1:])]
         self.rows = sum(w.rows for w in self.waves)

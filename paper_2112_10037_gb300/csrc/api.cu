@@ -29,6 +29,8 @@ struct spgemm_plan {
   int32_t* at_rp = nullptr;
   int32_t* at_ci = nullptr;
   int32_t* at_src = nullptr;
+  int32_t* a_row = nullptr;  // row of every nonzero of A (backward)
+  int32_t* b_row = nullptr;  // row of every entry of B (backward)
   // host state
   sg::PathBins pb{};
   sg::Tuning tu{};
@@ -56,7 +58,7 @@ inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 
 struct Layout {
   size_t st, prod, cmin, cmax, rows, cursor, nxt, scan, rr, runs, runs_part, hcnt, rrb, runsb;
-  size_t at_rp, at_ci, at_src, at_fill, at_tmp, at_part;  // opts.backward only
+  size_t at_rp, at_ci, at_src, at_fill, at_tmp, at_part, a_row, b_row;  // opts.backward only
   size_t total;
 };
 
@@ -186,6 +188,8 @@ Layout layout_for(const spgemm_opts& o, long long mloc, long long nnz_a, long lo
     L.at_rp = off; off = align_up(off + sizeof(int32_t) * (size_t)(nrows_b + 1));
     L.at_ci = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
     L.at_src = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
+    L.a_row = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
+    L.b_row = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_b);
     off = transpose_layout(off, nrows_b, nnz_a, &L.at_fill, &L.at_tmp, &L.at_part);
   }
   L.total = off;
@@ -240,6 +244,7 @@ void choose_paths(const spgemm_opts& o, sg::PathBins* pb, sg::Tuning* tu) {
   tu->hash_max = HASH_HI > 0 ? 1 << (HASH_HI - 1) : 0;
   tu->num_lo_block = numeric_block_bin(o);
   tu->num_lo_rank = numeric_rank_bin(o);
+  tu->rank_accum = o.rank_accum == 1 ? 1 : 0;
   const int TINY_HI = tiny_hi_bin(o);  // register sort up to opts.sort_max products
   const int SMALL_HI = small_hi_bin(o);
   const int wb = sg::bin_of(tu->warp_max) < SMALL_HI + 1 ? SMALL_HI + 1 : sg::bin_of(tu->warp_max);
@@ -391,6 +396,10 @@ static spgemm_status analyse_impl(const spgemm_csr* A, const spgemm_csr* B, cons
     int32_t* tmp = (int32_t*)(p->ws + L.at_tmp);
     e = sg::launch_transpose(c, A->nrows, A->ncols, A->nnz, A->row_ptr, A->col_idx, p->at_rp, p->at_ci, p->at_src,
                              (int32_t*)(p->ws + L.at_fill), tmp, tmp + A->nnz, (long long*)(p->ws + L.at_part));
+    p->a_row = (int32_t*)(p->ws + L.a_row);
+    p->b_row = (int32_t*)(p->ws + L.b_row);
+    if (e == cudaSuccess) e = sg::launch_row_index(c, A->row_ptr, A->nrows, p->a_row);
+    if (e == cudaSuccess) e = sg::launch_row_index(c, B->row_ptr, B->nrows, p->b_row);
   }
   if (e != cudaSuccess) { delete p; return SPGEMM_ERR_CUDA; }
   *plan = p;
@@ -417,7 +426,7 @@ void spgemm_opts_default(spgemm_opts* o) {
   o->block_warps = 0;
   o->sort_max = 0;
   o->rank_min = 0;
-  o->reserved = 0;
+  o->rank_accum = 0;
 }
 
 const char* spgemm_status_string(spgemm_status s) {
@@ -607,8 +616,8 @@ spgemm_status spgemm_backward(spgemm_plan* p, const void* a_vals, const void* b_
   if (db_vals && p->B.nnz > 0)
     e = cudaMemsetAsync(db_vals, 0, (size_t)p->B.nnz * (p->opts.dtype == SPGEMM_F32 ? 4 : 8), c.stream);
   if (e == cudaSuccess)
-    e = sg::launch_backward(c, p->opts.dtype, p->A, p->B, p->row_begin, p->mloc, a_vals, b_vals, p->at_rp, p->at_ci,
-                            p->at_src, c_row_ptr, c_col_idx, dc_vals, da_vals, db_vals);
+    e = sg::launch_backward(c, p->opts.dtype, p->A, p->B, p->row_begin, p->mloc, a_vals, b_vals, p->a_row, p->b_row,
+                            p->at_rp, p->at_ci, p->at_src, c_row_ptr, c_col_idx, dc_vals, da_vals, db_vals);
   return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 
@@ -963,10 +972,11 @@ spgemm_status spgemm_batch_products(int32_t n, const spgemm_csr* As, const spgem
 }
 
 spgemm_status spgemm_batch_waves(int32_t n, const spgemm_csr* As, const spgemm_csr* Bs, const int64_t* products,
-                                 int64_t max_products, int32_t* wave_first, int32_t* nwaves) {
+                                 int64_t max_products, int64_t max_b_nnz, int32_t* wave_first, int32_t* nwaves) {
   if (n < 0 || !wave_first || !nwaves || (n > 0 && (!As || !Bs || !products))) return SPGEMM_ERR_INVALID_ARG;
   const long long lim = (1ll << 31) - 1;  // stacked counts must stay below this (int32 indices)
   const long long pmax = (max_products > 0 && max_products < lim) ? max_products : lim;
+  const long long bmax = (max_b_nnz > 0 && max_b_nnz < lim) ? max_b_nnz : lim;
   long long rows = 0, ks = 0, ncols = 0, an = 0, bn = 0, pr = 0;
   int w = 0, count = 0;  // waves so far, instances in the open wave
   wave_first[0] = 0;
@@ -977,7 +987,8 @@ spgemm_status spgemm_batch_waves(int32_t n, const spgemm_csr* As, const spgemm_c
     if (As[i].ncols != Bs[i].nrows) return SPGEMM_ERR_DIM_MISMATCH;
     if (products[i] < 0) return SPGEMM_ERR_INVALID_ARG;
     const bool fits = rows + As[i].nrows < lim && ks + As[i].ncols < lim && ncols + Bs[i].ncols < lim &&
-                      an + As[i].nnz < lim && bn + Bs[i].nnz < lim && pr + products[i] <= pmax;
+                      an + As[i].nnz < lim && bn + Bs[i].nnz < lim && bn + Bs[i].nnz <= bmax &&
+                      pr + products[i] <= pmax;
     if (!fits && count > 0) {  // close the open wave
       wave_first[++w] = i;
       rows = ks = ncols = an = bn = pr = 0;

@@ -87,6 +87,7 @@ struct Tuning {
   int warp_max;        // largest P of the symbolic warp path
   int num_lo_block;    // numeric bins >= this use the block kernel (NBINS: never)
   int num_lo_rank;     // numeric bins >= this (below num_lo_block) use the rank kernel (NBINS: never)
+  int rank_accum;      // 0: rank kernel values reduced in global memory; 1: in shared-memory chunks
   int block_warps;     // warps per numeric block window
 };
 
@@ -289,10 +290,12 @@ cudaError_t launch_gather(const LaunchCtx& c, int dtype, const void* v, const in
 // C<M> = (A*B) .* M, mv null for the pattern only; mv is unused otherwise).
 cudaError_t launch_masked(const LaunchCtx& c, int dtype, int semiring, const Csr& A, const Csr& B, const Csr& M,
                           const void* av, const void* bv, const void* mv, void* out);
+// out[q] = row of entry q of a CSR with row pointer rp (nrows rows).
+cudaError_t launch_row_index(const LaunchCtx& c, const int32_t* rp, long long nrows, int32_t* out);
 cudaError_t launch_backward(const LaunchCtx& c, int dtype, const Csr& A, const Csr& B, long long row_begin,
-                            long long mloc, const void* av, const void* bv, const int32_t* t_rp,
-                            const int32_t* t_ci, const int32_t* t_src, const int32_t* c_rp,
-                            const int32_t* c_ci, const void* dc, void* da, void* db);
+                            long long mloc, const void* av, const void* bv, const int32_t* a_row,
+                            const int32_t* b_row, const int32_t* t_rp, const int32_t* t_ci, const int32_t* t_src,
+                            const int32_t* c_rp, const int32_t* c_ci, const void* dc, void* da, void* db);
 
 // One instance of a batched product (see batch.cu).
 struct BatchDesc {

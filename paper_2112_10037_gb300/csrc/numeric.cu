@@ -6,6 +6,7 @@
 #include "numrank.cuh"
 #include "numwarp.cuh"
 #include "rowhash.cuh"
+#include "rowlane.cuh"
 #include "rowpass.cuh"
 
 namespace sg {
@@ -128,16 +129,18 @@ static cudaError_t block_num(const LaunchCtx& c, const Csr& A, const Csr& B, con
   return cudaGetLastError();
 }
 
-// Rank-compacted accumulator: 8 warps per block, 6144 value slots (two
-// blocks of 104 KB share an SM in FP64).
+// Rank-compacted accumulator: 8 warps per block; values either reduced into
+// C in global memory (the default, 56 KB of shared memory per block, four
+// blocks per SM) or summed in shared memory 6144 ranks at a time (104 KB in
+// FP64, two blocks per SM).
 constexpr int RANK_WARPS = 8;
 constexpr int RANK_CAP = 6144;
 
-template <typename T>
+template <typename T, int CAP>
 static cudaError_t rank_num(const LaunchCtx& c, const Csr& A, const Csr& B, const T* av, const T* bv,
                             const RowInfo& ri, int lo, int hi, const int32_t* c_rp, int32_t* c_ci, T* c_v) {
-  auto k = k_num_rank<RANK_WARPS, RANK_CAP, T>;
-  const size_t smem = numrank_smem_bytes<RANK_WARPS, RANK_CAP, T>();
+  auto k = k_num_rank<RANK_WARPS, CAP, T>;
+  const size_t smem = numrank_smem_bytes<RANK_WARPS, CAP, T>();
   const int occ = kernel_blocks_per_sm(k, RANK_WARPS * 32, smem);
   if (occ <= 0) return cudaErrorInvalidConfiguration;
   unsigned* counter = &c.st->work[2];
@@ -190,10 +193,24 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
   if (pb.hi[PATH_HASH] >= pb.lo[PATH_HASH]) {
     const long long rows = rows_in(path_rows, PATH_HASH);
     timer_mark(c, T_NUM_HASH, 0);
-    e = hash_dispatch(hist, pb.lo[PATH_HASH], pb.hi[PATH_HASH],
-        [&](int l, int h) { return hash_num<T, 1>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
-        [&](int l, int h) { return hash_num<T, 2>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
-        [&](int l, int h) { return hash_num<T, 4>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); });
+    // When the hash rows are most of the product's rows (stencil and
+    // Galerkin products, where every row lands here), rows of at most 64
+    // products take one lane per row: throughput over many similar rows.
+    // A few such rows among larger ones (a power-law product) keep the warp
+    // per row, whose latency per row is lower.
+    long long all_rows = 0;
+    if (path_rows)
+      for (int q = 0; q < NPATHS; ++q) all_rows += path_rows[q];
+    const bool lanes = path_rows && 2 * (long long)path_rows[PATH_HASH] >= all_rows;
+    const int llo = pb.lo[PATH_HASH], lhi = lanes ? (pb.hi[PATH_HASH] < 7 ? pb.hi[PATH_HASH] : 7) : 0;
+    if (llo <= lhi && !empty_bins(hist, llo, lhi))
+      e = lane_rows<true, T>(c, A, B, av, bv, ri, llo, lhi, nullptr, c_rp, c_ci, c_v, rows);
+    const int wlo = lhi >= llo ? lhi + 1 : llo;
+    if (!e && pb.hi[PATH_HASH] >= wlo)
+      e = hash_dispatch(hist, wlo, pb.hi[PATH_HASH],
+          [&](int l, int h) { return hash_num<T, 1>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
+          [&](int l, int h) { return hash_num<T, 2>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); },
+          [&](int l, int h) { return hash_num<T, 4>(c, A, B, av, bv, ri, l, h, c_rp, c_ci, c_v, rows); });
     timer_mark(c, T_NUM_HASH, 1);
     if (e) return e;
   }
@@ -232,7 +249,8 @@ static cudaError_t numeric_t(const LaunchCtx& c, const Csr& A, const Csr& B, con
   if (!split && hi >= rlo) {
     if (!empty_bins(hist, rlo, hi)) {
       timer_mark(c, T_NUM_RANK, 0);
-      e = rank_num<T>(c, A, B, av, bv, ri, rlo, hi, c_rp, c_ci, c_v);
+      e = tu.rank_accum == 1 ? rank_num<T, RANK_CAP>(c, A, B, av, bv, ri, rlo, hi, c_rp, c_ci, c_v)
+                             : rank_num<T, 0>(c, A, B, av, bv, ri, rlo, hi, c_rp, c_ci, c_v);
       timer_mark(c, T_NUM_RANK, 1);
       if (e) return e;
     }

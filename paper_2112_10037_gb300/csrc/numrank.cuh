@@ -46,7 +46,8 @@ constexpr int RANK_GROUPS = RANK_WORDS >> RANK_GROUP_SHIFT;  // so they fit 16 b
 
 template <int NW, int CAP, typename T>
 __host__ __device__ constexpr size_t numrank_smem_bytes() {
-  return (size_t)CAP * sizeof(T)                     // compact values of one rank chunk
+  return (size_t)CAP * sizeof(T)                     // compact values of one rank chunk (none
+                                                     // when CAP == 0: values accumulate in C)
          + (size_t)nb_segcap<NW>() * sizeof(T)       // segment multipliers A(i,k)
          + (size_t)RANK_WORDS * 4                    // presence bitmap
          + (size_t)nb_segcap<NW>() * 8               // segment stream offsets and starts in B
@@ -108,11 +109,17 @@ __device__ __forceinline__ int rk_rank(const uint32_t* bits, const uint16_t* wpr
   return base + (int)wpre[w] + __popc(bits[w] & ((1u << (j & 31)) - 1u));
 }
 
+// acc += v on a global-memory word, result unused: the addition happens in
+// the L2 cache's atomic units, not in the SM's FP64 pipe.
+__device__ __forceinline__ void red_add_global(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add_global(float* p, float v) { atomicAdd(p, v); }
+
 // Stream products [lo, hi) of the list (tot products, nseg segments), software
 // pipelined as in nb_range.  MARK: set the columns' bits.  Otherwise: add the
-// products whose rank lies in [t0, t0 + chunk) into vals.  Every lane must
-// call it.
-template <bool MARK, typename T>
+// products whose rank lies in [t0, t0 + chunk) into vals (a shared-memory
+// array of chunk values), or with GLOBAL every product into vals[rank] (the
+// row's values in C, global memory).  Every lane must call it.
+template <bool MARK, typename T, bool GLOBAL = false>
 __device__ __forceinline__ void rk_range(const Csr& B, const T* __restrict__ bv, const int* off, const int* sstart,
                                          const T* sa, int nseg, int tot, int lo, int hi, int wbase, int wlen,
                                          uint32_t* bits, const uint16_t* wpre, int4 gp, T* vals, int t0,
@@ -132,6 +139,8 @@ __device__ __forceinline__ void rk_range(const Csr& B, const T* __restrict__ bv,
         if ((unsigned)j < (unsigned)wlen) {
           if (MARK) {
             atomicOr(&bits[j >> 5], 1u << (j & 31));
+          } else if (GLOBAL) {
+            red_add_global(&vals[rk_rank(bits, wpre, gp, j)], cur.a[u] * cur.b[u]);
           } else {
             const int rel = rk_rank(bits, wpre, gp, j) - t0;
             if ((unsigned)rel < (unsigned)chunk) fma_shared(&vals[rel], cur.a[u], cur.b[u], err);
@@ -178,7 +187,7 @@ __device__ __forceinline__ unsigned long long rk_list(const Csr& A, const Csr& B
 }
 
 template <int NW, int CAP, typename T>
-__global__ void __launch_bounds__(NW * 32, 2)
+__global__ void __launch_bounds__(NW * 32, CAP == 0 ? 3 : 2)
 k_num_rank(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri, const DevStats* st,
            int bin_lo, int bin_hi, const int32_t* __restrict__ c_rp, int32_t* __restrict__ c_ci,
            T* __restrict__ c_v, unsigned* counter, uint32_t* err) {
@@ -306,8 +315,37 @@ k_num_rank(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
           }
         }
       }
-      // 3. values, CAP ranks at a time
       const int4 gp = make_int4(s_gpre[0], s_gpre[1], s_gpre[2], s_gpre[3]);
+      if constexpr (CAP == 0) {
+        // 3. values added in global memory: the row's entries of C are
+        // zeroed (made visible before any reduction), then every product is
+        // reduced into its rank's entry in the L2 cache
+        const int nz = min(total, out_end - out);
+        for (int t = tid; t < nz; t += NT) rcv[out + t] = T(0);
+        __threadfence();
+        if (one_round) {
+          __syncthreads();
+          const int nseg = (int)(pk >> 32), tot = (int)(unsigned)(pk & 0xffffffffull);
+          const int share = ((tot + NT - 1) / NT) * 32;  // whole 32-product batches per warp
+          const int lo = warp * share, hi = min(tot, lo + share);
+          if (lo < hi && out + total <= out_end)
+            rk_range<false, T, true>(B, bv, seg_off, seg_s, seg_a, nseg, tot, lo, hi, (int)wbase, wlen, bits, wpre,
+                                     gp, rcv + out, 0, 0, err);
+        } else {
+          for (int r0 = a0; r0 < a1; r0 += SEGCAP) {
+            const unsigned long long pr = rk_list<NW, T>(A, B, av, r0, min(a1, r0 + SEGCAP), whole, (int)wbase,
+                                                         (int)wend, &s_pack, seg_off, seg_s, seg_a);
+            const int nseg = (int)(pr >> 32), tot = (int)(unsigned)(pr & 0xffffffffull);
+            const int share = ((tot + NT - 1) / NT) * 32;  // whole 32-product batches per warp
+            const int lo = warp * share, hi = min(tot, lo + share);
+            if (lo < hi && out + total <= out_end)
+              rk_range<false, T, true>(B, bv, seg_off, seg_s, seg_a, nseg, tot, lo, hi, (int)wbase, wlen, bits,
+                                       wpre, gp, rcv + out, 0, 0, err);
+            __syncthreads();
+          }
+        }
+      } else {
+      // 3. values, CAP ranks at a time
       for (int t0 = 0; t0 < total; t0 += CAP) {
         const int chunk = min(CAP, total - t0);
         for (int t = tid; t < chunk; t += NT) vals[t] = T(0);
@@ -338,6 +376,7 @@ k_num_rank(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
           if (p < out_end) __stcs(rcv + p, vals[t]);
         }
         __syncthreads();  // vals is cleared again by the next chunk
+      }
       }
       out += total;
       __syncthreads();  // the bitmap and offsets are rebuilt by the next window or row

@@ -2,6 +2,7 @@
 // (Sec. 2.2: the union of the columns of the B rows a row of A touches).
 #include "launch_util.cuh"
 #include "rowhash.cuh"
+#include "rowlane.cuh"
 #include "rowpass.cuh"
 #include "symblock.cuh"
 
@@ -122,10 +123,15 @@ cudaError_t launch_symbolic(const LaunchCtx& c, const Csr& A, const Csr& B, cons
   if (pb.hi[PATH_HASH] >= pb.lo[PATH_HASH]) {
     timer_mark(c, T_SYM_HASH, 0);
     const long long rows = rows_in(path_rows, PATH_HASH);
-    e = hash_dispatch(pb.lo[PATH_HASH], pb.hi[PATH_HASH],
-        [&](int l, int h) { return hash_sym<1>(c, A, B, ri, l, h, c_cnt, rows); },
-        [&](int l, int h) { return hash_sym<2>(c, A, B, ri, l, h, c_cnt, rows); },
-        [&](int l, int h) { return hash_sym<4>(c, A, B, ri, l, h, c_cnt, rows); });
+    // rows of at most 64 products: one lane per row; 65..128: a warp per row
+    const int llo = pb.lo[PATH_HASH], lhi = pb.hi[PATH_HASH] < 7 ? pb.hi[PATH_HASH] : 7;
+    if (llo <= lhi)
+      e = lane_rows<false, double>(c, A, B, nullptr, nullptr, ri, llo, lhi, c_cnt, nullptr, nullptr, nullptr, rows);
+    if (!e && pb.hi[PATH_HASH] >= 8)
+      e = hash_dispatch(8, pb.hi[PATH_HASH],
+          [&](int l, int h) { return hash_sym<1>(c, A, B, ri, l, h, c_cnt, rows); },
+          [&](int l, int h) { return hash_sym<2>(c, A, B, ri, l, h, c_cnt, rows); },
+          [&](int l, int h) { return hash_sym<4>(c, A, B, ri, l, h, c_cnt, rows); });
     timer_mark(c, T_SYM_HASH, 1);
     if (e) return e;
   }

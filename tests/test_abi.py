@@ -137,6 +137,8 @@ def test_batch_waves_host_only(libpath):
     assert nat.spgemm_batch_waves(As, Bs, prod, 1000) == [0, 7]
     assert nat.spgemm_batch_waves(As, Bs, prod, 0) == [0, 7]            # default bound 2^31 - 1
     assert nat.spgemm_batch_waves(As, Bs, [250] + prod[1:], 100)[:3] == [0, 1, 3]  # 250 alone
+    assert nat.spgemm_batch_waves(As, Bs, prod, 0, 90) == [0, 3, 6, 7]  # 30 B entries each, at most 90 a wave
+    assert nat.spgemm_batch_waves(As, Bs, prod, 100, 60)[:4] == [0, 2, 3, 4]  # both bounds
     assert nat.spgemm_batch_waves([], [], [], 0) == [0]
     # the default bound keeps every wave's product sum (an upper bound of its nnz(C)) inside int32
     big = [1 << 30, 1 << 30, 1 << 30, 5]

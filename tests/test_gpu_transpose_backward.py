@@ -122,6 +122,39 @@ def test_backward_vs_oracle(api, oracle_mod, seed, row_range):
     plan.close()
 
 
+@pytest.mark.parametrize("row_range", [None, (100, 9000)])
+def test_backward_power_law_rmat14(api, oracle_mod, row_range):
+    """Gradients of the R-MAT scale-14 product (hub rows of A and B with
+    thousands of entries, so sums of many more than 128 terms are split over
+    the warp and sums of a few terms stay in one lane) against the oracle's
+    gradient; a second call gives the same bits (fixed summation order)."""
+    A = gen.rmat(14, 16)
+    rng = np.random.default_rng(14)
+    A = gen.CSR(A.nrows, A.ncols, A.row_ptr, A.col_idx, rng.standard_normal(A.nnz))
+    dA = api.DeviceCSR.from_host(A)
+    kw = {} if row_range is None else {"row_range": row_range}
+    plan = api.Plan(dA, dA, backward=True, **kw)
+    rp, nnz = plan.symbolic()
+    plan.numeric(dA.vals, dA.vals)
+    W = rng.standard_normal(nnz)
+    dW = torch.from_numpy(W).cuda()
+    da, db = plan.backward(dA.vals, dA.vals, dW)
+    da2, db2 = plan.backward(dA.vals, dA.vals, dW)
+    torch.cuda.synchronize()
+    plan.check()
+    lo, hi = (0, A.nnz) if row_range is None else (int(A.row_ptr[row_range[0]]), int(A.row_ptr[row_range[1]]))
+    assert torch.equal(da[lo:hi], da2[lo:hi]) and torch.equal(db, db2)  # entries outside the range are not written
+    Asub = A if row_range is None else oracle_mod.select_rows(A, np.arange(*row_range))
+    C, rda, rdb = _grad_oracle(oracle_mod, Asub, A, W)
+    sa, sb = _scale_sums(oracle_mod, Asub, A, C, W)
+    got_da = da[lo:hi].cpu().numpy()
+    assert max_rel_err(got_da, rda, sa) <= 1e-12
+    assert max_rel_err(db.cpu().numpy(), rdb, sb) <= 1e-12
+    lens = np.diff(A.row_ptr.astype(np.int64))
+    assert lens.max() > 128 * 5  # the long-sum path is exercised on both gradients
+    plan.close()
+
+
 def test_autograd_finite_differences_fp64(api, oracle_mod):
     """L = sum W*C is bilinear: (L(a + h e_p) - L(a)) / h = dA[p] up to rounding."""
     A = gen.random_csr(60, 50, 0.1, 11)
