@@ -412,17 +412,36 @@ def fp64_peak_gflops(torch, dev):
     return round(sms * 2 * 2 * mhz * 1e6 / 1e9, 1)
 
 
+# Sources of the numeric pass's kernels: numeric.cu and everything it
+# includes.  A DRAM-traffic record stays valid while these are unchanged.
+NUMERIC_SOURCES = ["numeric.cu", "launch_util.cuh", "internal.cuh", "numblock.cuh", "numrank.cuh", "numwarp.cuh",
+                   "rowhash.cuh", "rowlane.cuh", "rowpass.cuh", "segstream.cuh"]
+
+
+def numeric_digest() -> str:
+    """16-hex-digit digest of the numeric kernels' sources and the ABI header."""
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(HERE, "paper_2112_10037_gb300", "csrc")
+    for name in NUMERIC_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode())
+            h.update(fh.read())
+    with open(os.path.join(HERE, "include", "spgemm.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profiles(kernel, workload):
     """dram read+write bytes per launch from a committed ncu summary, if one
-    exists for this kernel and workload and the sources have not changed
-    since; else None."""
+    exists for this kernel and workload and the numeric kernels' sources have
+    not changed since; else None."""
     path = os.path.join(HERE, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             rec = json.load(fh)
-        from paper_2112_10037_gb300 import build as bld
         ent = rec.get("%s|%s" % (kernel, workload))
-        if ent and ent.get("source_digest") == bld._deps_digest()[:16]:
+        if ent and ent.get("source_digest") == numeric_digest():
             return ent.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
