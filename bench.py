@@ -449,23 +449,27 @@ def traffic_from_profiles(kernel, workload):
 
 
 def run_e2e(args, api, torch, dev, A, B, kw, products):
-    """Same product through the public API with host buffers: pinned host
-    inputs copied to the device, then ``api.spgemm_to_host`` (row ranges
-    computed on the device while earlier ranges of C are copied back into
-    pinned host memory), all inside the timed region."""
+    """Same product end to end through the C ABI's host-buffer product
+    (``api.spgemm_host``: ``spgemm_host_product_begin`` / ``_finish``): A in
+    pinned host memory is copied to the device, C is sized, computed in row
+    ranges and copied back into pinned host memory while later ranges
+    compute -- all inside the timed region."""
+    kw = dict(kw)
+    rr = kw.pop("row_range", None)
+    aliased = B is A and rr is None   # A*A: B is not copied a second time
+    if rr is not None:  # this rank's row block of A
+        lo, hi = int(A.row_ptr[rr[0]]), int(A.row_ptr[rr[1]])
+        A = gen.CSR(rr[1] - rr[0], A.ncols, (A.row_ptr[rr[0]:rr[1] + 1] - lo).astype(np.int32), A.col_idx[lo:hi],
+                    A.vals[lo:hi])
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-    h_rp, h_ci, h_v = pin(A.row_ptr), pin(A.col_idx), pin(A.vals)
+    HA = gen.CSR(A.nrows, A.ncols, pin(A.row_ptr), pin(A.col_idx), pin(A.vals))
+    HB = None if aliased else gen.CSR(B.nrows, B.ncols, pin(B.row_ptr), pin(B.col_idx), pin(B.vals))
     stream = torch.cuda.current_stream()
     steps = max(3, min(args.steps, 5))
 
     def once(out=None, trace=None):
-        d_rp = h_rp.to(dev, non_blocking=True)
-        d_ci = h_ci.to(dev, non_blocking=True)
-        d_v = h_v.to(dev, non_blocking=True)
-        dA = api.DeviceCSR(A.nrows, A.ncols, d_rp, d_ci, d_v)
-        dB = dA if B is A else api.DeviceCSR.from_host(B, device=dev)
-        rp, ci, v = api.spgemm_to_host(dA, dB, dtype=torch.float64, chunks=args.e2e_chunks,
-                                       streams=args.e2e_streams, out=out, order=args.e2e_order, trace=trace, **kw)
+        rp, ci, v = api.spgemm_host(HA, HB, dtype=torch.float64, chunks=args.e2e_chunks, out=out, trace=trace,
+                                    device=dev, **kw)
         return (rp, ci, v), ci.numel(), rp.numel()
 
     # two untimed calls: the first pins the host buffers and allocates, the
@@ -486,6 +490,8 @@ def run_e2e(args, api, torch, dev, A, B, kw, products):
         traces.append(tr)
     ms = float(np.mean(ts))
     h2d = A.row_ptr.nbytes + A.col_idx.nbytes + A.vals.nbytes
+    if HB is not None:
+        h2d += B.row_ptr.nbytes + B.col_idx.nbytes + B.vals.nbytes
     d2h = 4 * nrp + 12 * nnz
 
     def summary(tr):

@@ -334,6 +334,56 @@ typedef enum spgemm_semiring_kind {
 spgemm_status spgemm_semiring(const spgemm_csr* A, const spgemm_csr* B, const spgemm_csr* M, int32_t dtype,
                               int32_t semiring, void* c_vals, spgemm_stream_t stream);
 
+/* ------------------------------------------------------- host buffers
+ * The whole product from host memory to host memory.  A and B are CSR with
+ * HOST pointers (pinned memory lets the copies overlap); C arrives in host
+ * arrays the caller allocates once nnz(C) is known.  Rows of C are
+ * independent (Sec. 2.2), so after one symbolic pass the numeric pass runs
+ * in row ranges of about equal output, each copied to the host on a second
+ * stream while the later ranges compute. */
+typedef struct spgemm_host_product spgemm_host_product;
+
+/* Device workspace of spgemm_host_product_begin: copies of A and B (one copy
+ * when B is A), C's row pointer and the plan of the whole product.  Host
+ * only. */
+spgemm_status spgemm_host_product_workspace_size(const spgemm_csr* A, const spgemm_csr* B,
+                                                 const spgemm_opts* opts, size_t* bytes);
+
+/* Copies A and B (host CSR, values of opts->dtype) into the workspace on
+ * `stream`, analyses the product, runs the symbolic pass and cuts the rows
+ * into at most `chunks` ranges of about equal output.  BLOCKS on `stream` to
+ * return nnz(C).  The workspace (device, 16-byte aligned) must stay valid
+ * until spgemm_host_product_destroy; the host inputs may be released on
+ * return.  opts: row_begin/row_end, backward and validate are ignored. */
+spgemm_status spgemm_host_product_begin(const spgemm_csr* A, const spgemm_csr* B, const spgemm_opts* opts,
+                                        int32_t chunks, void* workspace, size_t workspace_bytes,
+                                        spgemm_stream_t stream, spgemm_host_product** product, int64_t* nnz_c);
+
+/* Device staging bytes spgemm_host_product_finish needs: C's columns and
+ * values, and the workspaces of the row-range plans. */
+spgemm_status spgemm_host_product_staging_size(const spgemm_host_product* product, size_t* bytes);
+
+/* Numeric pass of every row range on `stream` into the staging buffer
+ * (device, 16-byte aligned), each range copied into c_col_idx / c_vals
+ * (host, nnz(C) entries) on copy_stream as soon as it is done (NULL:
+ * `stream`, no overlap); c_row_ptr (host, nrows(A) + 1 entries) receives C's
+ * row pointer.  BLOCKS until C is complete in host memory; reports any
+ * device error of the range plans.  Repeatable (the inputs' values are those
+ * copied by begin). */
+spgemm_status spgemm_host_product_finish(spgemm_host_product* product, int32_t* c_row_ptr, int32_t* c_col_idx,
+                                         void* c_vals, void* staging, size_t staging_bytes, spgemm_stream_t stream,
+                                         spgemm_stream_t copy_stream);
+
+/* Number of row ranges, and the device timeline of the last finish: for
+ * range r, ms[4r .. 4r+3] = its numeric pass's start and end and its copy's
+ * start and end, in milliseconds from the start of the first range (entries
+ * past the ranges read 0). */
+spgemm_status spgemm_host_product_ranges(const spgemm_host_product* product, int32_t* nranges);
+spgemm_status spgemm_host_product_timeline(const spgemm_host_product* product, float* ms, int32_t n);
+
+/* Frees the handle and its plan (host memory only).  NULL is allowed. */
+void spgemm_host_product_destroy(spgemm_host_product* product);
+
 /* Frees the plan (host memory only).  NULL is allowed. */
 void spgemm_plan_destroy(spgemm_plan* plan);
 

@@ -103,6 +103,15 @@ _SIG = {
                             ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int32),
                             ctypes.POINTER(ctypes.c_int32)],
                            ctypes.c_int),
+    "spgemm_host_product_workspace_size": ([ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr),
+                                            ctypes.POINTER(spgemm_opts), ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "spgemm_host_product_begin": ([ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_csr), ctypes.POINTER(spgemm_opts),
+                                   ctypes.c_int32, _P, ctypes.c_size_t, _P, ctypes.POINTER(_P), _I64P], ctypes.c_int),
+    "spgemm_host_product_staging_size": ([_P, ctypes.POINTER(ctypes.c_size_t)], ctypes.c_int),
+    "spgemm_host_product_finish": ([_P, _P, _P, _P, _P, ctypes.c_size_t, _P, _P], ctypes.c_int),
+    "spgemm_host_product_ranges": ([_P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "spgemm_host_product_timeline": ([_P, ctypes.POINTER(ctypes.c_float), ctypes.c_int32], ctypes.c_int),
+    "spgemm_host_product_destroy": ([_P], None),
     "spgemm_batch_plan": ([_P], _P),
     "spgemm_batch_destroy": ([_P], None),
 }
@@ -366,3 +375,51 @@ def spgemm_semiring(A: spgemm_csr, B: spgemm_csr, M: spgemm_csr, dtype: int, sem
                     stream: int) -> None:
     _check(lib().spgemm_semiring(ctypes.byref(A), ctypes.byref(B), ctypes.byref(M), dtype, semiring, _P(c_vals),
                                  _P(stream)), "spgemm_semiring")
+
+
+def spgemm_host_product_workspace_size(A: spgemm_csr, B: spgemm_csr, opts: spgemm_opts) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().spgemm_host_product_workspace_size(ctypes.byref(A), ctypes.byref(B), ctypes.byref(opts),
+                                                    ctypes.byref(n)), "spgemm_host_product_workspace_size")
+    return n.value
+
+
+def spgemm_host_product_begin(A: spgemm_csr, B: spgemm_csr, opts: spgemm_opts, chunks: int, workspace: int,
+                              workspace_bytes: int, stream: int):
+    """(handle, nnz(C))."""
+    h = _P(None)
+    nnz = ctypes.c_int64(-1)
+    _check(lib().spgemm_host_product_begin(ctypes.byref(A), ctypes.byref(B), ctypes.byref(opts), int(chunks),
+                                           _P(workspace), ctypes.c_size_t(workspace_bytes), _P(stream),
+                                           ctypes.byref(h), ctypes.byref(nnz)), "spgemm_host_product_begin")
+    return h.value, nnz.value
+
+
+def spgemm_host_product_staging_size(product: int) -> int:
+    n = ctypes.c_size_t(0)
+    _check(lib().spgemm_host_product_staging_size(_P(product), ctypes.byref(n)), "spgemm_host_product_staging_size")
+    return n.value
+
+
+def spgemm_host_product_finish(product: int, c_row_ptr: int, c_col_idx: int, c_vals: int, staging: int,
+                               staging_bytes: int, stream: int, copy_stream: int) -> None:
+    _check(lib().spgemm_host_product_finish(_P(product), _P(c_row_ptr), _P(c_col_idx), _P(c_vals), _P(staging),
+                                            ctypes.c_size_t(staging_bytes), _P(stream), _P(copy_stream)),
+           "spgemm_host_product_finish")
+
+
+def spgemm_host_product_ranges(product: int) -> int:
+    n = ctypes.c_int32(0)
+    _check(lib().spgemm_host_product_ranges(_P(product), ctypes.byref(n)), "spgemm_host_product_ranges")
+    return n.value
+
+
+def spgemm_host_product_timeline(product: int, n: int):
+    ms = (ctypes.c_float * max(n, 1))()
+    _check(lib().spgemm_host_product_timeline(_P(product), ms, int(n)), "spgemm_host_product_timeline")
+    return list(ms)[:n]
+
+
+def spgemm_host_product_destroy(product: int) -> None:
+    if product:
+        lib().spgemm_host_product_destroy(_P(product))

@@ -393,6 +393,95 @@ def _spgemm_to_host(A: DeviceCSR, B: DeviceCSR, dtype=torch.float64, chunks: int
     return h_rp[:m + 1], h_ci[:total], h_v[:total]
 
 
+_host_buffers = {}
+
+
+def _host_array(x, np_dtype):
+    """A contiguous host array of np_dtype for x (numpy array or CPU tensor;
+    converted only when needed, pinned tensors pass through)."""
+    if isinstance(x, torch.Tensor):
+        assert x.device.type == "cpu"
+        t = x if x.dtype == torch.from_numpy(np.zeros(0, np_dtype)).dtype else x.to(
+            torch.from_numpy(np.zeros(0, np_dtype)).dtype)
+        return t.contiguous()
+    return np.ascontiguousarray(x, dtype=np_dtype)
+
+
+def _host_struct(M, dtype):
+    """(spgemm_csr of a host CSR, the arrays it points into, to keep alive)."""
+    vt = np.float64 if dtype == torch.float64 else np.float32
+    rp, ci, v = _host_array(M.row_ptr, np.int32), _host_array(M.col_idx, np.int32), _host_array(M.vals, vt)
+    ptr = lambda a: a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+    s = nat.spgemm_csr()
+    s.nrows, s.ncols = int(M.nrows), int(M.ncols)
+    s.nnz = int(rp[-1]) if int(M.nrows) > 0 else 0
+    s.row_ptr = ptr(rp)
+    s.col_idx = ptr(ci) if s.nnz else 0
+    s.vals = ptr(v) if s.nnz else 0
+    return s, (rp, ci, v)
+
+
+def _device_buffer(dev, name, nbytes):
+    key = (dev.index, name)
+    buf = _host_buffers.get(key)
+    if buf is None or buf.numel() < max(nbytes, 16):
+        _host_buffers.pop(key, None)
+        buf = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=dev)
+        _host_buffers[key] = buf
+    return buf
+
+
+def spgemm_host(A, B=None, dtype=torch.float64, chunks: int = 4, out=None, trace=None, device=None, **opt_kw):
+    """C = A*B from host memory to host memory through the C ABI's
+    host-buffer product (``spgemm_host_product_begin`` / ``_finish``): the
+    inputs are copied to the device, one symbolic pass sizes C, and the
+    numeric pass runs in ``chunks`` row ranges of about equal output, each
+    copied back while the later ones compute.  A, B: host CSR (``gen.CSR``
+    or objects with nrows / ncols / row_ptr / col_idx / vals as numpy arrays
+    or CPU tensors -- pinned memory for overlapped copies -- values already
+    of ``dtype``); B defaults to A (copied once).  ``out`` = (row_ptr,
+    col_idx, vals) pinned CPU tensors to fill, reused when large enough.
+    ``trace``: a dict that receives host marks (ms after the call's start
+    when begin -- copies in, analysis, symbolic pass -- and finish returned)
+    and the per-range device timeline.  Returns
+    CPU tensors (row_ptr, col_idx, vals).  Calls on one device share the
+    device buffers, so they are serialised."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    t0 = time.perf_counter()
+    with _staging_lock:
+        sa, keep_a = _host_struct(A, dtype)
+        sb, keep_b = (sa, keep_a) if B is None or B is A else _host_struct(B, dtype)
+        opts = make_opts(dtype=dtype, **opt_kw)
+        nbytes = nat.spgemm_host_product_workspace_size(sa, sb, opts)
+        ws = _device_buffer(dev, "workspace", nbytes)
+        stream = torch.cuda.current_stream(dev)
+        copy = _stream_pool(dev, "copy", 1)[0]
+        h, nnz = nat.spgemm_host_product_begin(sa, sb, opts, int(chunks), ws.data_ptr(), nbytes,
+                                               int(stream.cuda_stream))
+        t_begin = time.perf_counter()
+        try:
+            st_bytes = nat.spgemm_host_product_staging_size(h)
+            stg = _device_buffer(dev, "staging", st_bytes)
+            m = int(A.nrows)
+            if out is None or out[0].numel() < m + 1 or out[1].numel() < nnz or out[2].numel() < nnz:
+                out = (torch.empty(m + 1, dtype=torch.int32).pin_memory(),
+                       torch.empty(max(nnz, 1), dtype=torch.int32).pin_memory(),
+                       torch.empty(max(nnz, 1), dtype=dtype).pin_memory())
+            h_rp, h_ci, h_v = out
+            nat.spgemm_host_product_finish(h, h_rp.data_ptr(), h_ci.data_ptr(), h_v.data_ptr(), stg.data_ptr(),
+                                           st_bytes, int(stream.cuda_stream), int(copy.cuda_stream))
+            if trace is not None:
+                nr = nat.spgemm_host_product_ranges(h)
+                tl = nat.spgemm_host_product_timeline(h, 4 * nr)
+                ms = lambda t: round((t - t0) * 1e3, 3)
+                trace.update({"host_ms": {"begin_returned": ms(t_begin), "finish_returned": ms(time.perf_counter())},
+                              "device_ms": {"numeric_start": tl[0::4], "numeric_end": tl[1::4],
+                                            "copy_start": tl[2::4], "copy_end": tl[3::4]}})
+        finally:
+            nat.spgemm_host_product_destroy(h)
+    return h_rp[:m + 1], h_ci[:nnz], h_v[:nnz]
+
+
 def transpose(M: DeviceCSR, want_src: bool = False, dtype=None, stream=None):
     """M^T as a DeviceCSR (``spgemm_transpose``); with ``want_src`` also the
     int32 source positions (t_vals[q] = M.vals[src[q]])."""

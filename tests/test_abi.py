@@ -166,3 +166,48 @@ def test_batch_products_host_checks_without_gpu(libpath):
         nat.spgemm_batch_products([_desc(4, 5, 0)], [_desc(6, 3, 0)], 256, 256, 1 << 12, 0)
     assert ei.value.status == 2
     nat.spgemm_batch_products([], [], 0, 0, 0, 0)  # nothing to count
+
+
+def test_host_product_host_checks_without_gpu(libpath):
+    """The host-buffer product sizes its workspace on the host (one copy of
+    the inputs when B is A) and rejects bad arguments before any copy."""
+    o = nat.spgemm_opts_default()
+
+    def csr(m, n, nnz, base):
+        M = nat.spgemm_csr()
+        M.nrows, M.ncols, M.nnz = m, n, nnz
+        M.row_ptr, M.col_idx, M.vals = base, base + 4096, base + 8192  # never dereferenced here
+        return M
+
+    A = csr(1000, 1000, 50000, 1 << 20)
+    B = csr(1000, 1000, 50000, 1 << 24)
+    same = nat.spgemm_host_product_workspace_size(A, A, o)
+    both = nat.spgemm_host_product_workspace_size(A, B, o)
+    # B's arrays (row pointer, columns, FP64 values) are the difference
+    assert both - same >= 4 * 1001 + 12 * 50000
+    o32 = nat.spgemm_opts_default()
+    o32.dtype = nat.SPGEMM_F32
+    assert nat.spgemm_host_product_workspace_size(A, B, o32) < both
+    bad = csr(999, 1000, 50000, 1 << 26)
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_host_product_workspace_size(A, bad, o)
+    assert ei.value.status == 2  # A.ncols != B.nrows
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_host_product_begin(A, B, o, 0, 1 << 30, both, 0)
+    assert ei.value.status == 1  # chunks < 1
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_host_product_begin(A, B, o, 4, 0, both, 0)
+    assert ei.value.status == 5  # no workspace
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_host_product_begin(A, B, o, 4, 1 << 30, both - 1, 0)
+    assert ei.value.status == 5  # workspace too small
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_host_product_begin(A, B, o, 4, (1 << 30) + 8, both, 0)
+    assert ei.value.status == 5  # workspace not 16-byte aligned
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_host_product_staging_size(0)
+    assert ei.value.status == 1
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_host_product_finish(0, 1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 20, 0, 0)
+    assert ei.value.status == 1
+    nat.spgemm_host_product_destroy(0)

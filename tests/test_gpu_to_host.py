@@ -99,3 +99,65 @@ def test_adopt_refuses_split_rows(api):
         pl.adopt(rp, nnz)
     pl.close()
     base.close()
+
+
+@pytest.mark.parametrize("chunks", [1, 4, 33])
+def test_host_product_rmat_aliased(api, oracle_mod, chunks):
+    """Host CSR in, host CSR out through spgemm_host_product_begin/finish,
+    B aliased to A (one copy), against the oracle; the device timeline has
+    one numeric and one copy interval per row range, in order."""
+    A = gen.rmat(12, 8)
+    tr = {}
+    rp, ci, v = api.spgemm_host(A, chunks=chunks, trace=tr)
+    C = _host_csr(A.nrows, A.ncols, rp.numpy(), ci.numpy(), v.numpy())
+    R, S = oracle_with_scale(oracle_mod, A, A)
+    assert_structure_equal(C, R)
+    assert_values_close(C.vals, R.vals, S)
+    d = tr["device_ms"]
+    nr = len(d["numeric_start"])
+    assert 1 <= nr <= chunks
+    for r in range(nr):
+        assert d["numeric_start"][r] <= d["numeric_end"][r] <= d["copy_start"][r] + 1e-3
+        assert d["copy_start"][r] <= d["copy_end"][r]
+        if r:
+            assert d["numeric_start"][r] >= d["numeric_end"][r - 1] - 1e-3
+
+
+def test_host_product_rectangular_pinned_reused(api, oracle_mod):
+    """Distinct A and B (rectangular, empty rows, integer values: exact) from
+    pinned host tensors; a second call fills the first call's output."""
+    rng = np.random.default_rng(11)
+    counts = rng.integers(0, 9, size=700)
+    counts[::5] = 0
+    A = gen.random_rows(700, 300, counts, rng, values="int")
+    B = gen.random_rows(300, 9000, rng.integers(0, 60, size=300), rng, values="int")
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    HA = gen.CSR(A.nrows, A.ncols, pin(A.row_ptr), pin(A.col_idx), pin(A.vals))
+    HB = gen.CSR(B.nrows, B.ncols, pin(B.row_ptr), pin(B.col_idx), pin(B.vals))
+    R = oracle_mod.spgemm(A, B)
+    out = None
+    for chunks in (6, 2):
+        rp, ci, v = api.spgemm_host(HA, HB, chunks=chunks, out=out)
+        if out is None:
+            out = (rp, ci, v)
+        else:
+            assert ci.data_ptr() == out[1].data_ptr()
+        C = _host_csr(A.nrows, B.ncols, rp.numpy(), ci.numpy(), v.numpy())
+        assert_structure_equal(C, R)
+        assert_values_exact(C.vals, R.vals)
+
+
+def test_host_product_fp32_and_empty(api, oracle_mod):
+    """FP32 values (the oracle's FP64 result rounded, within FP32 error), and
+    an empty product."""
+    A = gen.laplacian_2d(30)
+    A32 = gen.CSR(A.nrows, A.ncols, A.row_ptr, A.col_idx, A.vals.astype(np.float32))
+    rp, ci, v = api.spgemm_host(A32, dtype=torch.float32, chunks=3)
+    R = oracle_mod.spgemm(A, A)
+    C = _host_csr(A.nrows, A.ncols, rp.numpy(), ci.numpy(), v.numpy())
+    assert_structure_equal(C, R)
+    np.testing.assert_allclose(C.vals, R.vals, rtol=1e-6, atol=1e-6)
+    E = gen.CSR(50, 40, np.zeros(51, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    F = gen.CSR(40, 30, np.zeros(41, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    rp, ci, v = api.spgemm_host(E, F, chunks=4)
+    assert rp.numel() == 51 and int(rp.abs().sum()) == 0 and ci.numel() == 0 and v.numel() == 0
