@@ -251,11 +251,12 @@ spgemm_status spgemm_transpose_workspace_size(int64_t nrows, int64_t ncols, int6
 /* M^T in CSR (Sec. 2.1: M's CSC form): t_row_ptr (ncols+1 entries),
  * t_col_idx (nnz; each row ascending), t_vals (nnz values of `dtype`, or NULL
  * for structure only), t_src (nnz source positions in M, or NULL), so that
- * t_vals[q] = M.vals[t_src[q]].  Column indices of M must be in range and,
- * as for every input of this library, ascending and unique within each row
- * (columns of M with more than 8192 entries rely on it).  Does not block;
- * spgemm_transpose_check reads the error word: SPGEMM_ERR_UNSORTED_INPUT for
- * a column index out of range or a repeated column found in a long column. */
+ * t_vals[q] = M.vals[t_src[q]].  Column indices of M must be in range; the
+ * transpose does not rely on their order within a row (it is a stable sort
+ * of M's entries by column, so every row of M^T is ascending by source row;
+ * a column repeated in a row of M gives that source row twice, adjacent).
+ * Does not block; spgemm_transpose_check reads the error word:
+ * SPGEMM_ERR_UNSORTED_INPUT for a column index out of range. */
 spgemm_status spgemm_transpose(const spgemm_csr* M, int32_t dtype, int32_t* t_row_ptr, int32_t* t_col_idx,
                                void* t_vals, int32_t* t_src, void* workspace, size_t workspace_bytes,
                                spgemm_stream_t stream);
@@ -274,9 +275,14 @@ spgemm_status spgemm_transpose_check(void* workspace, spgemm_stream_t stream);
  * Its scratch is one fixed 8 MiB device array inside this library, present
  * on every GPU that loads the library until the process exits.  Inputs whose
  * scratch would exceed it are rejected with SPGEMM_ERR_WORKSPACE: the need
- * is 8*nnz bytes (12*nnz when t_src is NULL, which then also needs scratch)
- * + 4*ncols + 8*ncols/4096 bytes plus about 2 KB of bookkeeping and
- * alignment, so about 1 M entries fit with t_src given.  The inputs follow
+ * is, for 513 to 262,144 columns, 12*nnz bytes plus 8*nnz (FP64) or 4*nnz
+ * (FP32) when t_vals is given (none of this for at most 512 columns; 4*nnz
+ * more above 262,144 columns), plus 4*nnz when t_src is NULL (the source
+ * positions then need scratch too), plus the digit counts (4 bytes per
+ * digit value and 4096 entries: at most nnz/2 bytes) and their scan partials
+ * (8 bytes per 4096 counts or columns), plus about 2 KB of bookkeeping and
+ * alignment; so about 400 K entries fit with t_src and FP64 t_vals given.
+ * The inputs follow
  * spgemm_transpose's preconditions.  The first call on a device looks
  * up the array's device address; make that first call before any stream
  * capture.  All calls on a device share the array (each call clears what

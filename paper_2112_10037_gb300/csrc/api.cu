@@ -58,16 +58,18 @@ inline size_t align_up(size_t x) { return (x + ALIGN - 1) & ~(ALIGN - 1); }
 
 struct Layout {
   size_t st, prod, cmin, cmax, rows, cursor, nxt, scan, rr, runs, runs_part, hcnt, rrb, runsb;
-  size_t at_rp, at_ci, at_src, at_fill, at_tmp, at_part, a_row, b_row;  // opts.backward only
+  size_t at_rp, at_ci, at_src, at_tmp, at_table, at_part, a_row, b_row;  // opts.backward only
   size_t total;
 };
 
 // Workspace of a transpose of an m x n matrix with nnz entries, at offset
 // `off`; returns the end offset.
-size_t transpose_layout(size_t off, long long n, long long nnz, size_t* fill, size_t* tmp, size_t* part) {
-  *fill = off; off = align_up(off + sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
-  *tmp = off; off = align_up(off + 2 * sizeof(int32_t) * (size_t)nnz);
-  *part = off; off = align_up(off + sizeof(long long) * sg::scan_partials_count(n));
+size_t transpose_layout(size_t off, long long n, long long nnz, int vbytes, size_t* tmp, size_t* table,
+                        size_t* part) {
+  const sg::TransposeScratch s = sg::transpose_scratch(n, nnz, vbytes);
+  *tmp = off; off = align_up(off + sizeof(int32_t) * s.tmp_ints);
+  *table = off; off = align_up(off + sizeof(int32_t) * s.table_ints);
+  *part = off; off = align_up(off + sizeof(long long) * s.part_count);
   return off;
 }
 
@@ -190,7 +192,7 @@ Layout layout_for(const spgemm_opts& o, long long mloc, long long nnz_a, long lo
     L.at_src = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
     L.a_row = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_a);
     L.b_row = off; off = align_up(off + sizeof(int32_t) * (size_t)nnz_b);
-    off = transpose_layout(off, nrows_b, nnz_a, &L.at_fill, &L.at_tmp, &L.at_part);
+    off = transpose_layout(off, nrows_b, nnz_a, 0, &L.at_tmp, &L.at_table, &L.at_part);
   }
   L.total = off;
   return L;
@@ -393,9 +395,9 @@ static spgemm_status analyse_impl(const spgemm_csr* A, const spgemm_csr* B, cons
     p->at_rp = (int32_t*)(p->ws + L.at_rp);
     p->at_ci = (int32_t*)(p->ws + L.at_ci);
     p->at_src = (int32_t*)(p->ws + L.at_src);
-    int32_t* tmp = (int32_t*)(p->ws + L.at_tmp);
     e = sg::launch_transpose(c, A->nrows, A->ncols, A->nnz, A->row_ptr, A->col_idx, p->at_rp, p->at_ci, p->at_src,
-                             (int32_t*)(p->ws + L.at_fill), tmp, tmp + A->nnz, (long long*)(p->ws + L.at_part));
+                             0, nullptr, nullptr, (int32_t*)(p->ws + L.at_tmp), (int32_t*)(p->ws + L.at_table),
+                             (long long*)(p->ws + L.at_part));
     p->a_row = (int32_t*)(p->ws + L.a_row);
     p->b_row = (int32_t*)(p->ws + L.b_row);
     if (e == cudaSuccess) e = sg::launch_row_index(c, A->row_ptr, A->nrows, p->a_row);
@@ -624,10 +626,10 @@ spgemm_status spgemm_backward(spgemm_plan* p, const void* a_vals, const void* b_
 spgemm_status spgemm_transpose_workspace_size(int64_t nrows, int64_t ncols, int64_t nnz, size_t* bytes) {
   if (!bytes || nrows < 0 || ncols < 0 || nnz < 0) return SPGEMM_ERR_INVALID_ARG;
   if (nnz >= (1ll << 31) || ncols >= (1ll << 31) - 1) return SPGEMM_ERR_INDEX_OVERFLOW;
-  size_t fill, tmp, part;
+  size_t tmp, table, part;
   size_t off = align_up(sizeof(sg::DevStats));
   off = align_up(off + sizeof(int32_t) * (size_t)nnz);  // source positions if the caller wants none
-  *bytes = transpose_layout(off, ncols, nnz, &fill, &tmp, &part);
+  *bytes = transpose_layout(off, ncols, nnz, 8, &tmp, &table, &part);  // room for FP64 values
   return SPGEMM_OK;
 }
 
@@ -653,15 +655,15 @@ spgemm_status spgemm_transpose(const spgemm_csr* M, int32_t dtype, int32_t* t_ro
   size_t off = align_up(sizeof(sg::DevStats));
   int32_t* own_src = (int32_t*)(ws + off);
   off = align_up(off + sizeof(int32_t) * (size_t)M->nnz);
-  size_t fill, tmp, part;
-  transpose_layout(off, M->ncols, M->nnz, &fill, &tmp, &part);
+  size_t tmp, table, part;
+  transpose_layout(off, M->ncols, M->nnz, 8, &tmp, &table, &part);
   int32_t* src = t_src ? t_src : own_src;
-  int32_t* tmpp = (int32_t*)(ws + tmp);
+  const int vbytes = t_vals ? (dtype == SPGEMM_F32 ? 4 : 8) : 0;
   cudaError_t e = cudaMemsetAsync(c.st, 0, sizeof(sg::DevStats), c.stream);
   if (e == cudaSuccess)
     e = sg::launch_transpose(c, M->nrows, M->ncols, M->nnz, M->row_ptr, M->col_idx, t_row_ptr, t_col_idx, src,
-                             (int32_t*)(ws + fill), tmpp, tmpp + M->nnz, (long long*)(ws + part));
-  if (e == cudaSuccess && t_vals) e = sg::launch_gather(c, dtype, M->vals, src, t_vals, M->nnz);
+                             vbytes, M->vals, t_vals, (int32_t*)(ws + tmp), (int32_t*)(ws + table),
+                             (long long*)(ws + part));
   return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 

@@ -282,10 +282,18 @@ cudaError_t launch_numeric(const LaunchCtx& c, const Csr& A, const Csr& B, const
                            const int* hist /* host rows per bin, may be null: bins without rows
                                               are not launched */);
 
+// Scratch of a transpose of a matrix with n columns and nnz entries whose
+// values have vbytes bytes (0: structure only): tmp (int32), the digit table
+// (int32) and the scan partials (int64).
+struct TransposeScratch {
+  size_t tmp_ints, table_ints, part_count;
+};
+TransposeScratch transpose_scratch(long long n, long long nnz, int vbytes);
+// M^T: t_rp (n+1), t_ci and t_src (nnz, required), and with vbytes 4 or 8
+// and both value pointers, t_vals[q] = vals[t_src[q]].
 cudaError_t launch_transpose(const LaunchCtx& c, long long m, long long n, long long nnz, const int32_t* rp,
-                             const int32_t* ci, int32_t* t_rp, int32_t* t_ci, int32_t* t_src, int32_t* fill,
-                             int32_t* tmp_ci, int32_t* tmp_src, long long* partials);
-cudaError_t launch_gather(const LaunchCtx& c, int dtype, const void* v, const int32_t* src, void* out, long long nnz);
+                             const int32_t* ci, int32_t* t_rp, int32_t* t_ci, int32_t* t_src, int vbytes,
+                             const void* vals, void* t_vals, int32_t* tmp, int32_t* table, long long* partials);
 // Masked product on M's pattern over a semiring (spgemm_semiring; 0 is
 // C<M> = (A*B) .* M, mv null for the pattern only; mv is unused otherwise).
 cudaError_t launch_masked(const LaunchCtx& c, int dtype, int semiring, const Csr& A, const Csr& B, const Csr& M,

@@ -32,19 +32,21 @@ constexpr size_t NA_ALIGN = 256;
 inline size_t na_align(size_t x) { return (x + NA_ALIGN - 1) & ~(NA_ALIGN - 1); }
 
 struct NaLayout {
-  size_t st, src, fill, tmp, part, total;
+  size_t st, src, tmp, table, part, total;
 };
 
-// The source positions get scratch only when the caller passes no t_src.
-NaLayout na_layout(long long ncols, long long nnz, bool need_src) {
+// The source positions get scratch only when the caller passes no t_src;
+// values (vbytes each, 0 without t_vals) travel through the scratch.
+NaLayout na_layout(long long ncols, long long nnz, bool need_src, int vbytes) {
+  const TransposeScratch s = transpose_scratch(ncols, nnz, vbytes);
   NaLayout L{};
   size_t off = 0;
   L.st = off; off = na_align(off + sizeof(DevStats));
   L.src = off;
   if (need_src) off = na_align(off + sizeof(int32_t) * (size_t)nnz);
-  L.fill = off; off = na_align(off + sizeof(int32_t) * (size_t)(ncols > 0 ? ncols : 1));
-  L.tmp = off; off = na_align(off + 2 * sizeof(int32_t) * (size_t)nnz);
-  L.part = off; off = na_align(off + sizeof(long long) * scan_partials_count(ncols));
+  L.tmp = off; off = na_align(off + sizeof(int32_t) * s.tmp_ints);
+  L.table = off; off = na_align(off + sizeof(int32_t) * s.table_ints);
+  L.part = off; off = na_align(off + sizeof(long long) * s.part_count);
   L.total = off;
   return L;
 }
@@ -88,7 +90,8 @@ extern "C" spgemm_status spgemm_transpose_noalloc(const spgemm_csr* M, int32_t d
   if (!t_row_ptr || (M->nnz > 0 && !t_col_idx)) return SPGEMM_ERR_INVALID_ARG;
   if (dtype != SPGEMM_F64 && dtype != SPGEMM_F32) return SPGEMM_ERR_INVALID_ARG;
   if (t_vals && M->nnz > 0 && !M->vals) return SPGEMM_ERR_INVALID_ARG;
-  const NaLayout L = na_layout(M->ncols, M->nnz, t_src == nullptr);
+  const int vbytes = t_vals ? (dtype == SPGEMM_F32 ? 4 : 8) : 0;
+  const NaLayout L = na_layout(M->ncols, M->nnz, t_src == nullptr, vbytes);
   if (L.total > NOALLOC_SCRATCH_BYTES) return SPGEMM_ERR_WORKSPACE;  // does not fit the fixed scratch
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return SPGEMM_ERR_CUDA;
@@ -101,12 +104,11 @@ extern "C" spgemm_status spgemm_transpose_noalloc(const spgemm_csr* M, int32_t d
   c.st = (DevStats*)(ws + L.st);
   c.err = &c.st->err;
   int32_t* src = t_src ? t_src : (int32_t*)(ws + L.src);
-  int32_t* tmp = (int32_t*)(ws + L.tmp);
   // the stats word (error bits, scan total) must start at zero every call
   cudaError_t e = cudaMemsetAsync(c.st, 0, sizeof(DevStats), c.stream);
   if (e == cudaSuccess)
     e = launch_transpose(c, M->nrows, M->ncols, M->nnz, M->row_ptr, M->col_idx, t_row_ptr, t_col_idx, src,
-                         (int32_t*)(ws + L.fill), tmp, tmp + M->nnz, (long long*)(ws + L.part));
-  if (e == cudaSuccess && t_vals) e = launch_gather(c, dtype, M->vals, src, t_vals, M->nnz);
+                         vbytes, M->vals, t_vals, (int32_t*)(ws + L.tmp), (int32_t*)(ws + L.table),
+                         (long long*)(ws + L.part));
   return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }

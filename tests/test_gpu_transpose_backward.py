@@ -35,7 +35,8 @@ def test_transpose_vs_oracle(api, oracle_mod, shape, density, seed):
 
 
 def test_transpose_long_columns(api, oracle_mod):
-    """Columns with > 32 and > 8192 entries take the block sorts."""
+    """A 20,000-entry column (its row of M^T spans several tiles of the
+    counting scatter) among short ones."""
     rng = np.random.default_rng(0)
     m = 20000
     counts = rng.integers(1, 6, size=m)
@@ -67,19 +68,55 @@ def test_transpose_long_column_spanning_windows(api, oracle_mod):
     assert int(np.diff(R.row_ptr)[0]) == 12_000
 
 
-def test_transpose_repeated_column_in_long_column_is_reported(api):
-    """A row of M that repeats a column breaks the input precondition; in a
-    column of more than 8192 entries the transpose reports it as unsorted
-    input instead of returning a row with unwritten entries."""
-    m = 9000
-    rows = [np.array([0, 0, 5]) if i == 17 else np.array([0, 1 + i % 7]) for i in range(m)]
+def test_transpose_repeated_and_unsorted_columns(api):
+    """The transpose is a stable sort of M's entries by column, so it needs
+    neither ascending nor unique columns within a row of M: a repeated column
+    gives its source row twice, adjacent, and every row of M^T is ascending
+    by source row.  Checked against numpy's stable argsort."""
+    rng = np.random.default_rng(5)
+    m, n = 9000, 700
+    rows = [rng.integers(0, n, size=rng.integers(0, 9)) for _ in range(m)]  # unsorted, repeats allowed
+    rows[17] = np.array([0, 0, 5, 0])
     rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
     ci = np.concatenate(rows).astype(np.int32)
-    M = gen.CSR(m, 8, rp, ci, np.ones(len(ci)))
+    v = rng.standard_normal(len(ci))
+    M = gen.CSR(m, n, rp, ci, v)
+    T, src = api.transpose(api.DeviceCSR.from_host(M), want_src=True)
+    order = np.argsort(ci, kind="stable")
+    row_of = np.repeat(np.arange(m, dtype=np.int32), np.diff(rp))
+    got = T.to_host()
+    assert np.array_equal(got.row_ptr, np.concatenate([[0], np.cumsum(np.bincount(ci, minlength=n))]))
+    assert np.array_equal(got.col_idx, row_of[order])
+    assert np.array_equal(src.cpu().numpy(), order)
+    assert np.array_equal(got.vals, v[order])
+    first0 = got.col_idx[got.row_ptr[0]:got.row_ptr[1]]
+    assert int((first0 == 17).sum()) == 3
+
+
+def test_transpose_column_out_of_range_is_reported(api):
+    M = gen.CSR(3, 4, np.array([0, 1, 2, 3], np.int32), np.array([1, 4, 2], np.int32), np.ones(3))
     from paper_2112_10037_gb300 import _native as nat
     with pytest.raises(nat.SpgemmError) as ei:
         api.transpose(api.DeviceCSR.from_host(M))
     assert ei.value.status == 3
+
+
+@pytest.mark.parametrize("ncols", [1, 512, 513, 65536, 262144, 262145, 3_000_000])
+def test_transpose_digit_passes(api, oracle_mod, ncols):
+    """One to three counting-scatter passes (at most 9 bits of the column
+    index each: 1 pass up to 512 columns, 2 up to 262,144, 3 above), with
+    more entries than one 4096-entry tile and a ragged last tile."""
+    rng = np.random.default_rng(ncols)
+    m = 5000
+    counts = rng.integers(0, 12, size=m)
+    counts[::97] = 0
+    M = gen.random_rows(m, ncols, np.minimum(counts, ncols), rng)
+    T, src = api.transpose(api.DeviceCSR.from_host(M), want_src=True)
+    R = oracle_mod.transpose(M)
+    got = T.to_host()
+    assert_structure_equal(got, R)
+    assert np.array_equal(got.vals, R.vals)
+    assert np.array_equal(M.vals[src.cpu().numpy()], R.vals)
 
 
 def _grad_oracle(oracle_mod, A, B, W):

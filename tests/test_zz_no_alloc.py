@@ -81,7 +81,8 @@ def test_noalloc_transpose_long_columns_and_repeat(mods):
 
 def test_noalloc_long_column_spanning_windows(mods):
     """A 12,000-entry column over 600,000 source rows (its transpose row
-    crosses a 262,144-key window of the long-row sort), twice in a row."""
+    gathers entries from every tile of the counting scatter), twice in a
+    row."""
     nat, api = mods
     from parity import long_column_matrix
     dM = api.DeviceCSR.from_host(long_column_matrix())
@@ -93,13 +94,16 @@ def test_noalloc_long_column_spanning_windows(mods):
 
 
 def test_noalloc_size_rule_with_and_without_t_src(mods):
-    """An input whose scratch fits with t_src given (8 bytes per entry) but
-    not without it (12 bytes per entry) runs in the first case and is
-    refused in the second."""
+    """An input of 1000 columns (two counting-scatter passes of 5 bits) whose
+    scratch fits with t_src and FP64 t_vals given (12 + 8 bytes per entry
+    plus the digit counts) but not without t_src (4 bytes per entry more)
+    runs in the first case and is refused in the second; without values
+    and without t_src (16 bytes per entry) it runs again."""
     nat, api = mods
-    M = gen.random_csr(9000, 1000, 0.1, 7)
+    M = gen.random_csr(9000, 1000, 0.043, 7)
     limit = 8 << 20
-    assert 8 * M.nnz + 4 * M.ncols + 4096 < limit < 12 * M.nnz
+    tiles = (M.nnz + 4095) // 4096
+    assert 20 * M.nnz + 4 * (32 * tiles + 1) + 8 * 64 + 4096 < limit < 24 * M.nnz
     dM = api.DeviceCSR.from_host(M)
     T, src = _reference(nat, api, dM)
     rp2, ci2, v2, s2 = _noalloc(nat, api, dM)
@@ -107,10 +111,16 @@ def test_noalloc_size_rule_with_and_without_t_src(mods):
     assert torch.equal(v2, T.vals) and torch.equal(s2, src)
     t_rp = torch.empty(M.ncols + 1, dtype=torch.int32, device=dM.row_ptr.device)
     t_ci = torch.empty(M.nnz, dtype=torch.int32, device=dM.row_ptr.device)
+    t_v = torch.empty(M.nnz, dtype=torch.float64, device=dM.row_ptr.device)
     with pytest.raises(nat.SpgemmError) as ei:
-        nat.spgemm_transpose_noalloc(dM.c_struct(), nat.SPGEMM_F64, t_rp.data_ptr(), t_ci.data_ptr(), 0, 0,
-                                     int(torch.cuda.current_stream().cuda_stream))
+        nat.spgemm_transpose_noalloc(dM.c_struct(), nat.SPGEMM_F64, t_rp.data_ptr(), t_ci.data_ptr(),
+                                     t_v.data_ptr(), 0, int(torch.cuda.current_stream().cuda_stream))
     assert ei.value.status == 5
+    # structure only and no t_src: 16 bytes per entry, which fits
+    nat.spgemm_transpose_noalloc(dM.c_struct(), nat.SPGEMM_F64, t_rp.data_ptr(), t_ci.data_ptr(), 0, 0,
+                                 int(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert torch.equal(t_rp, T.row_ptr) and torch.equal(t_ci, T.col_idx)
 
 
 def test_noalloc_rejects_inputs_beyond_the_fixed_scratch(mods):
