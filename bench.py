@@ -1047,9 +1047,10 @@ def run_omar(args):
 def run_variants(args):
     """The widened products on the 3D stencil 96^3 (A*A) and on R-MAT
     scale 16 (A*A): the column-wise Gustavson product (transposes around a
-    row-wise product, all three steps timed), and the semiring values
-    (min-plus, max-plus, or-and) on the pattern of A*B, timed without the
-    pattern's own computation.  GFLOP/s counts 2 FLOP per product formed."""
+    row-wise product, all three steps timed), and the semiring products
+    (min-plus, max-plus, or-and): the whole product (symbolic and numeric
+    passes), its numeric pass alone, and the masked product on the pattern
+    of A*B.  GFLOP/s counts 2 FLOP per product formed."""
     import torch
     from paper_2112_10037_gb300 import api, build as bld
     bld.build()
@@ -1068,13 +1069,26 @@ def run_variants(args):
         C = api.spgemm(dM, dM)
         P = api.DeviceCSR(C.nrows, C.ncols, C.row_ptr, C.col_idx, None)
         for sr in ("min_plus", "max_plus", "or_and"):
+            # the semiring product itself: symbolic + numeric with the
+            # semiring's accumulators, and its numeric pass alone
+            for _ in range(args.warmup):
+                api.spgemm_semiring(dM, dM, sr)
+            ms, _ = _events_ms(lambda: api.spgemm_semiring(dM, dM, sr), args.steps, stream)
+            plan = api.Plan(dM, dM, semiring=sr)
+            plan.symbolic()
+            for _ in range(args.warmup):
+                plan.numeric(dM.vals, dM.vals)
+            ms_num, _ = _events_ms(lambda: plan.numeric(dM.vals, dM.vals), args.steps, stream)
+            plan.close()
+            # the masked product on the same pattern (values only)
             for _ in range(args.warmup):
                 api.masked_semiring(dM, dM, P, sr)
-            ms, _ = _events_ms(lambda: api.masked_semiring(dM, dM, P, sr), args.steps, stream)
-            entry[sr] = {"ms": round(ms, 4), "gflops": round(2.0 * products / (ms / 1e3) / 1e9, 2)}
+            ms_mask, _ = _events_ms(lambda: api.masked_semiring(dM, dM, P, sr), args.steps, stream)
+            entry[sr] = {"ms": round(ms, 4), "gflops": round(2.0 * products / (ms / 1e3) / 1e9, 2),
+                         "numeric_ms": round(ms_num, 4), "masked_ms": round(ms_mask, 4)}
         res[name] = entry
     first = res["laplacian3d_96"]
-    out = _base_line("SpGEMM GFLOP/s (2*products/s), min-plus values on the product's pattern",
+    out = _base_line("SpGEMM GFLOP/s (2*products/s), min-plus product (symbolic and numeric passes)",
                      first["min_plus"]["gflops"], "GFLOP/s", args, first["min_plus"]["ms"],
                      {"workload": "variants_laplacian3d_96_and_rmat_s16"})
     out["matrices"] = res

@@ -119,6 +119,15 @@ typedef struct spgemm_opts {
                           in C itself, zeroed first, by reductions in the L2 cache's atomic
                           units; 1 in shared memory, 6144 ranks per pass over the row's
                           products */
+  int32_t semiring;    /* sum and product of the numeric pass (spgemm_semiring_kind below):
+                          SPGEMM_PLUS_TIMES (0, the default) or min-plus, max-plus, or-and,
+                          each row of C then the semiring sum over A(i,k) of the products
+                          A(i,k) (x) B(k,:) on the same pattern (Sec. 2.2 with + and *
+                          replaced; min, max and or do not depend on the order of the sums,
+                          so those values are exact).  With another semiring sort_max,
+                          rank_min, split_min, window_warp, window_block and block_warps
+                          are ignored (defaults; no rank-compacted accumulator, no split
+                          rows), and backward must be 0 */
 } spgemm_opts;
 
 typedef struct spgemm_plan spgemm_plan;

@@ -45,7 +45,8 @@ class spgemm_opts(ctypes.Structure):
                 ("window_block", ctypes.c_int32), ("split_min", ctypes.c_int32),
                 ("backward", ctypes.c_int32), ("num_block_min", ctypes.c_int32),
                 ("block_warps", ctypes.c_int32), ("sort_max", ctypes.c_int32),
-                ("rank_min", ctypes.c_int32), ("rank_accum", ctypes.c_int32)]
+                ("rank_min", ctypes.c_int32), ("rank_accum", ctypes.c_int32),
+                ("semiring", ctypes.c_int32)]
 
 
 _lib = None

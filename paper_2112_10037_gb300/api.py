@@ -66,7 +66,8 @@ def _stream_handle(stream=None) -> int:
 
 def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1, warp_max=0,
               window_warp=0, window_block=0, split_min=0, backward=False, num_block_min=0,
-              block_warps=0, sort_max=0, hash_max=0, rank_min=0, rank_accum=0) -> nat.spgemm_opts:
+              block_warps=0, sort_max=0, hash_max=0, rank_min=0, rank_accum=0,
+              semiring="plus_times") -> nat.spgemm_opts:
     o = nat.spgemm_opts_default()
     o.dtype = _DT[dtype]
     o.validate = 1 if validate else 0
@@ -84,6 +85,7 @@ def make_opts(dtype=torch.float64, validate=False, row_range=None, force_path=-1
     o.hash_max = int(hash_max)
     o.rank_min = int(rank_min)
     o.rank_accum = int(rank_accum)
+    o.semiring = SEMIRINGS[semiring] if isinstance(semiring, str) else int(semiring)
     return o
 
 
@@ -538,16 +540,15 @@ def masked_semiring(A: DeviceCSR, B: DeviceCSR, M: DeviceCSR, semiring: str = "m
 
 
 def spgemm_semiring(A: DeviceCSR, B: DeviceCSR, semiring: str = "min_plus", dtype=None, **opt_kw) -> DeviceCSR:
-    """C = A (x) B over a semiring on the full pattern of A*B (the product's
-    structure from the symbolic and numeric passes, then the semiring values
-    on it)."""
+    """C = A (x) B over a semiring on the full pattern of A*B: one symbolic
+    pass and one numeric pass whose accumulators use the semiring's sum and
+    product (the plan option ``semiring``)."""
     dtype = dtype or A.vals.dtype
-    plan = Plan(A, B, dtype=dtype, **opt_kw)
+    plan = Plan(A, B, dtype=dtype, semiring=semiring, **opt_kw)
     rp, _ = plan.symbolic()
-    ci, _ = plan.numeric(A.vals, B.vals)
+    ci, v = plan.numeric(A.vals, B.vals)
     plan.close()
-    P = DeviceCSR(plan.nrows, B.ncols, rp, ci, None)
-    return DeviceCSR(plan.nrows, B.ncols, rp, ci, masked_semiring(A, B, P, semiring, dtype=dtype))
+    return DeviceCSR(plan.nrows, B.ncols, rp, ci, v)
 
 
 def _plan_backward(self, a_vals, b_vals, dc_vals, need_a=True, need_b=True):

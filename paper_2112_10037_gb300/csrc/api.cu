@@ -325,6 +325,18 @@ static spgemm_status analyse_impl(const spgemm_csr* A, const spgemm_csr* B, cons
   if (opts) o = *opts; else spgemm_opts_default(&o);
   if (o.dtype != SPGEMM_F64 && o.dtype != SPGEMM_F32) return SPGEMM_ERR_INVALID_ARG;
   if (o.force_path < -1 || o.force_path > 4) return SPGEMM_ERR_INVALID_ARG;
+  if (o.semiring < SPGEMM_PLUS_TIMES || o.semiring > SPGEMM_OR_AND) return SPGEMM_ERR_INVALID_ARG;
+  if (o.semiring != SPGEMM_PLUS_TIMES) {
+    // other semirings skip the rank-compacted accumulator, register sorts
+    // above 128 products, split rows and the non-default window sizes
+    if (o.backward) return SPGEMM_ERR_INVALID_ARG;
+    o.sort_max = 0;
+    o.rank_min = -1;
+    o.split_min = -1;
+    o.window_warp = 0;
+    o.window_block = 0;
+    o.block_warps = 0;
+  }
   const long long rb = o.row_begin, re = o.row_end < 0 ? A->nrows : o.row_end;
   if (rb < 0 || re < rb || re > A->nrows) return SPGEMM_ERR_DIM_MISMATCH;
   const Layout L = layout_for(o, re - rb, A->nnz, B->nrows, B->ncols, B->nnz, base == nullptr);
@@ -552,7 +564,7 @@ spgemm_status spgemm_numeric(spgemm_plan* p, const void* a_vals, const void* b_v
   const sg::RowInfo ri = rowinfo_of(p);
   cudaError_t e = sg::launch_numeric(c, p->A, p->B, ri, p->pb, p->tu, p->sp, p->opts.dtype, a_vals, b_vals,
                                      p->cursor, p->nxt, c_row_ptr, c_col_idx, c_vals, p->path_rows,
-                                     (long long)p->host_st.rows_wide, p->host_st.hist);
+                                     (long long)p->host_st.rows_wide, p->host_st.hist, p->opts.semiring);
   return e == cudaSuccess ? SPGEMM_OK : SPGEMM_ERR_CUDA;
 }
 

@@ -280,7 +280,17 @@ cudaError_t launch_numeric(const LaunchCtx& c, const Csr& A, const Csr& B, const
                            const int* path_rows /* host, may be null */,
                            long long rows_wide /* rows with more than 32 nonzeros, -1: unknown */,
                            const int* hist /* host rows per bin, may be null: bins without rows
-                                              are not launched */);
+                                              are not launched */,
+                           int semiring /* spgemm_semiring_kind */);
+// The numeric pass over the min-plus, max-plus and or-and semirings.
+#define SG_NUMERIC_SR_DECL(NAME)                                                                              \
+  cudaError_t NAME(const LaunchCtx& c, const Csr& A, const Csr& B, const RowInfo& ri, const PathBins& pb,     \
+                   const Tuning& tu, const SplitInfo& sp, int dtype, const void* av, const void* bv,          \
+                   int32_t* cur, int32_t* nxt, const int32_t* c_rp, int32_t* c_ci, void* c_v,                 \
+                   const int* path_rows, long long rows_wide, const int* hist)
+SG_NUMERIC_SR_DECL(launch_numeric_min_plus);
+SG_NUMERIC_SR_DECL(launch_numeric_max_plus);
+SG_NUMERIC_SR_DECL(launch_numeric_or_and);
 
 // Scratch of a transpose of a matrix with n columns and nnz entries whose
 // values have vbytes bytes (0: structure only): tmp (int32), the digit table

@@ -25,6 +25,7 @@
 #pragma once
 
 #include "segstream.cuh"
+#include "semiring.cuh"
 
 namespace sg {
 
@@ -101,11 +102,11 @@ __device__ __forceinline__ void nb_load(const Csr& B, const T* __restrict__ bv, 
 
 // One product: acc[col - base] += a * b, the column marked present on its
 // first update.
-template <int W, typename T>
+template <int W, typename T, int SR>
 __device__ __forceinline__ void nb_add(int col, T a, T b, int base, T* acc, uint32_t* bits, uint32_t* err) {
   const int j = col - base;
   if ((unsigned)j < (unsigned)W) {
-    if (fma_shared(&acc[j], a, b, err)) atomicOr(&bits[j >> 5], 1u << (j & 31));
+    if (SrOps<T, SR>::madd_shared(&acc[j], a, b, err)) atomicOr(&bits[j >> 5], 1u << (j & 31));
   } else {
     atomicOr(err, EB_UNSORTED);
   }
@@ -117,7 +118,7 @@ __device__ __forceinline__ void nb_add(int col, T a, T b, int base, T* acc, uint
 // measured 2.4 % faster than two on R-MAT 18; walking long segments directly
 // instead of through the stream mapping was 4 % slower).  hi - lo is a
 // multiple of 32 unless hi == tot.  Every lane must call it.
-template <int W, typename T, int U = 3>
+template <int W, typename T, int U = 3, int SR = SPGEMM_PLUS_TIMES>
 __device__ __forceinline__ void nb_range(const Csr& B, const T* __restrict__ bv, const int* off, const int* sstart,
                                          const T* sa, int nseg, int tot, int lo, int hi, int base, T* acc,
                                          uint32_t* bits, uint32_t* err) {
@@ -130,7 +131,7 @@ __device__ __forceinline__ void nb_range(const Csr& B, const T* __restrict__ bv,
     if (p0 + 32 * U < hi) nb_load<U, T>(B, bv, off, sstart, sa, nseg, tot, hi, p0 + 32 * U, f, nxt);
 #pragma unroll
     for (int u = 0; u < U; ++u)
-      if (p0 + 32 * u + lane < hi) nb_add<W, T>(cur.col[u], cur.a[u], cur.b[u], base, acc, bits, err);
+      if (p0 + 32 * u + lane < hi) nb_add<W, T, SR>(cur.col[u], cur.a[u], cur.b[u], base, acc, bits, err);
     cur = nxt;
   }
 }
@@ -143,7 +144,7 @@ __device__ __forceinline__ void nb_range(const Csr& B, const T* __restrict__ bv,
 // coalesced.  An output's chunk comes from a warp search over the chunk
 // offsets, its word from a binary search over the chunk's offsets, its bit
 // from a binary search on popcounts inside the word.  Every lane must call it.
-template <int NW, int WPW, typename T>
+template <int NW, int WPW, typename T, int SR>
 __device__ __forceinline__ void nb_emit(const uint32_t* bits, const uint16_t* wpre, const int* wcnt, T* acc, int base,
                                         int out, int out_end, int32_t* __restrict__ rci, T* __restrict__ rcv,
                                         uint32_t* err) {
@@ -179,7 +180,7 @@ __device__ __forceinline__ void nb_emit(const uint32_t* bits, const uint16_t* wp
       const int jj = (word << 5) + bit;
       const int pos = out + t;
       const T v = acc[jj];
-      acc[jj] = T(0);
+      acc[jj] = SrOps<T, SR>::zero();
       if (pos < out_end) {
         __stcs(rci + pos, base + jj);
         __stcs(rcv + pos, v);
@@ -203,7 +204,7 @@ __host__ __device__ constexpr int nb_blocks_per_sm() {
 
 // rrb/runsb: B's run list at the block window's granularity (log2 W), so the
 // segment of B(k,:) in a block window is exactly one run.
-template <int W, int NW, typename T>
+template <int W, int NW, typename T, int SR = SPGEMM_PLUS_TIMES>
 __global__ void __launch_bounds__(NW * 32, nb_blocks_per_sm<W, NW, T>())
 k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri, const DevStats* st,
             int bin_lo, int bin_hi, const int32_t* __restrict__ rrb, const int2* __restrict__ runsb,
@@ -235,7 +236,7 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
   // one can be cleared while the other is read
   __shared__ unsigned long long s_pack[2];
   const int warp = threadIdx.x >> 5, lane = lane_id();
-  for (int t = threadIdx.x; t < W; t += NW * 32) acc[t] = T(0);
+  for (int t = threadIdx.x; t < W; t += NW * 32) acc[t] = SrOps<T, SR>::zero();
   for (int t = threadIdx.x; t < 2 * NWORDS; t += NW * 32) bits0[t] = 0u;
   if (threadIdx.x == 0) {
     bin_range(st, bin_lo, bin_hi, &s_lb, &s_le);
@@ -349,7 +350,7 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
         {  // each warp takes a contiguous share of the stream, whole batches
           const int share = ((tot + NW * 32 - 1) / (NW * 32)) * 32;
           const int lo = warp * share, hi = min(tot, lo + share);
-          if (lo < hi) nb_range<W, T>(B, bv, seg_off, seg_s, seg_a, nseg, tot, lo, hi, base, acc, bits, err);
+          if (lo < hi) nb_range<W, T, 3, SR>(B, bv, seg_off, seg_s, seg_a, nseg, tot, lo, hi, base, acc, bits, err);
         }
         __syncthreads();  // all products in; the list may be refilled
         parity ^= 1;
@@ -375,7 +376,7 @@ k_num_block(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
         total += wcnt[w];
         nb = min(nb, wnext[w]);
       }
-      nb_emit<NW, WPW, T>(bits, wpre, wcnt, acc, base, out, out_end, rci, rcv, err);
+      nb_emit<NW, WPW, T, SR>(bits, wpre, wcnt, acc, base, out, out_end, rci, rcv, err);
       out += total;
       // no barrier: the next window's list barrier orders this emission
       // before its products (which use the other bitmap, and find the

@@ -28,6 +28,7 @@
 #pragma once
 
 #include "internal.cuh"
+#include "semiring.cuh"
 
 namespace sg {
 
@@ -44,8 +45,9 @@ struct NumSplit {
 
 constexpr int NW_SLOTS = 8;  // register cursors: up to 256 nonzeros of A per row
 
-template <int W, typename T>
+template <int W, typename T, int SR = SPGEMM_PLUS_TIMES>
 struct WarpWin {
+  using Ops = SrOps<T, SR>;
   T* acc;
   uint32_t* bits;   // presence bitmap, W / 32 words
   uint32_t* err;
@@ -59,8 +61,8 @@ struct WarpWin {
     if (act) {
       if ((unsigned)j < (unsigned)W) {
         const T old = acc[j];
-        acc[j] = fma(a, b, old);
-        if (is_cleared(old)) mark(j);
+        acc[j] = Ops::madd(a, b, old);
+        if (Ops::cleared(old)) mark(j);
       } else {
         atomicOr(err, EB_UNSORTED);
       }
@@ -76,7 +78,7 @@ struct WarpWin {
     if (act) {
       if ((unsigned)j < (unsigned)W) {
         mark(j);
-        red_add_shared(&acc[j], a * b);
+        Ops::red_shared(&acc[j], a, b, err);
       } else {
         atomicOr(err, EB_UNSORTED);
       }
@@ -226,7 +228,7 @@ struct WarpWin {
           }
           const int jj = ((wb + o) << 5) + bit;
           const T v = acc[jj];
-          acc[jj] = T(0);
+          acc[jj] = Ops::zero();
           const int pos = out + total + t;
           if (pos < out_end) {
             __stcs(c_ci + pos, base + jj);
@@ -262,7 +264,7 @@ __device__ __forceinline__ int lower_bound_run(const int2* __restrict__ runs, in
   return lo;
 }
 
-template <int W, int NWARP, typename T>
+template <int W, int NWARP, typename T, int SR = SPGEMM_PLUS_TIMES>
 __global__ void __launch_bounds__(NWARP * 32)
 k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri, const DevStats* st,
            int bin_lo, int bin_hi, NumSplit sp, int32_t* __restrict__ gcur, int32_t* __restrict__ gnxt,
@@ -275,11 +277,11 @@ k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_lb, s_le, s_nh;
   const int warp = threadIdx.x >> 5, lane = lane_id();
-  WarpWin<W, T> win;
+  WarpWin<W, T, SR> win;
   win.acc = reinterpret_cast<T*>(smem_raw + (size_t)warp * WB);
   win.bits = reinterpret_cast<uint32_t*>(smem_raw + (size_t)warp * WB + (size_t)W * sizeof(T));
   win.err = err;
-  for (int t = lane; t < W; t += 32) win.acc[t] = T(0);
+  for (int t = lane; t < W; t += 32) win.acc[t] = SrOps<T, SR>::zero();
   for (int t = lane; t < W / 32; t += 32) win.bits[t] = 0u;
   if (threadIdx.x == 0) {
     int b, e;
@@ -465,7 +467,7 @@ k_num_warp(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
 // window: its short-segment products are placed and their loads issued
 // before this window's products are accumulated and emitted, which hide
 // their latency.  Same accumulator, emission and result as k_num_warp.
-template <int W, int NWARP, typename T>
+template <int W, int NWARP, typename T, int SR = SPGEMM_PLUS_TIMES>
 __global__ void __launch_bounds__(NWARP * 32, W <= 1024 ? 3 : 1)
 k_num_warp1(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri, const DevStats* st,
             int bin_lo, int bin_hi, NumSplit sp, const int32_t* __restrict__ c_rp, int32_t* __restrict__ c_ci,
@@ -476,11 +478,11 @@ k_num_warp1(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int s_lb, s_le, s_nh;
   const int warp = threadIdx.x >> 5, lane = lane_id();
-  WarpWin<W, T> win;
+  WarpWin<W, T, SR> win;
   win.acc = reinterpret_cast<T*>(smem_raw + (size_t)warp * WB);
   win.bits = reinterpret_cast<uint32_t*>(smem_raw + (size_t)warp * WB + (size_t)W * sizeof(T));
   win.err = err;
-  for (int t = lane; t < W; t += 32) win.acc[t] = T(0);
+  for (int t = lane; t < W; t += 32) win.acc[t] = SrOps<T, SR>::zero();
   for (int t = lane; t < W / 32; t += 32) win.bits[t] = 0u;
   if (threadIdx.x == 0) {
     int b, e;
@@ -534,7 +536,7 @@ k_num_warp1(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
       }
     }
     int w = warp_min(wid);
-    typename WarpWin<W, T>::Flat f;
+    typename WarpWin<W, T, SR>::Flat f;
     if (w != INT_MAX) win.flat_gather(B, bv, s0, wid == w ? s1 - s0 : 0, a, w << WSHIFT, f);
     int out = 0;
     while (w != INT_MAX) {
@@ -551,7 +553,7 @@ k_num_warp1(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
       // flight while this window is accumulated and emitted
       const int wid1 = act ? nwid : wid, s01 = act ? ns0 : s0, s11 = act ? ns1 : s1;
       const int wn = warp_min(wid1);
-      typename WarpWin<W, T>::Flat fn;
+      typename WarpWin<W, T, SR>::Flat fn;
       if (wn != INT_MAX) win.flat_gather(B, bv, s01, wid1 == wn ? s11 - s01 : 0, a, wn << WSHIFT, fn);
       const int len = act ? s1 - s0 : 0;
       win.long_segments(B, bv, s0, len, a, base);

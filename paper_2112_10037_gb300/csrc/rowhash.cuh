@@ -23,6 +23,7 @@
 #pragma once
 
 #include "internal.cuh"
+#include "semiring.cuh"
 
 namespace sg {
 
@@ -85,7 +86,7 @@ __device__ __forceinline__ void b_bounds(const Csr& B, int k, int* sb, int* len)
 // preloaded in c0; later chunks (rows of more than 32 nonzeros) load their
 // own.  NUM: pv = A(i,k) * B(k,j), one rounded multiply per product.  Empty
 // slots hold column INT_MAX.  Returns the row's product count.
-template <int E, bool NUM, typename T>
+template <int E, bool NUM, typename T, int SR = SPGEMM_PLUS_TIMES>
 __device__ __forceinline__ int hash_gather(const Csr& A, const Csr& B, const T* __restrict__ av,
                                            const T* __restrict__ bv, int a0, int a1, const Chunk0<T>& c0,
                                            int (&col)[E], T (&pv)[E]) {
@@ -124,7 +125,7 @@ __device__ __forceinline__ int hash_gather(const Csr& A, const Csr& B, const T* 
       if (q >= 0 && q < tot) {
         const int bi = os + q - oex;
         col[s] = B.ci[bi];
-        if (NUM) pv[s] = oa * bv[bi];
+        if (NUM) pv[s] = SrOps<T, SR>::mul(oa, bv[bi]);
       }
     }
     done += tot;
@@ -235,7 +236,7 @@ k_hash_sym(Csr A, Csr B, RowInfo ri, const DevStats* st, int bin_lo, int bin_hi,
 // positions [c_rp[r], c_rp[r+1]) the symbolic pass and the scan fixed.
 // The product that claims a column's slot stores its value there; the
 // others add theirs with a shared-memory reduction after a warp barrier.
-template <int E, typename T>
+template <int E, typename T, int SR = SPGEMM_PLUS_TIMES>
 __global__ void __launch_bounds__(HASH_WARPS * 32)
 k_hash_num(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri, const DevStats* st,
            int bin_lo, int bin_hi, const int32_t* __restrict__ c_rp, int32_t* __restrict__ c_ci,
@@ -263,7 +264,7 @@ k_hash_num(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
     const int ob = c_rp[r], oe = c_rp[r + 1];
     int col[E];
     T pv[E];
-    const int P = hash_gather<E, true, T>(A, B, av, bv, a0, a1, c0, col, pv);
+    const int P = hash_gather<E, true, T, SR>(A, B, av, bv, a0, a1, c0, col, pv);
     if (P > 32 * E && lane == 0) atomicOr(err, EB_INTERNAL);  // the row's bin rules this out
     int slot[E];
     bool fresh[E];
@@ -279,7 +280,7 @@ k_hash_num(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Row
     __syncwarp();
 #pragma unroll
     for (int s = 0; s < E; ++s)
-      if (!fresh[s] && slot[s] >= 0) red_add_shared(&val[slot[s]], pv[s]);
+      if (!fresh[s] && slot[s] >= 0) SrOps<T, SR>::red_value(&val[slot[s]], pv[s], err);
     __syncwarp();
     // Compaction: the occupied slots, in slot order, into the list dk/dv;
     // each slot's key is cleared by the lane that read it.

@@ -25,6 +25,7 @@
 #pragma once
 
 #include "launch_util.cuh"
+#include "semiring.cuh"
 
 namespace sg {
 
@@ -56,7 +57,7 @@ __device__ __forceinline__ int lane_probe(int* keys, int lane, int j, bool* fres
 
 // NUM = false: c_cnt[r] = distinct columns of row r.  NUM = true: C's
 // columns and values at [c_rp[r], c_rp[r+1]).
-template <bool NUM, typename T>
+template <bool NUM, typename T, int SR = SPGEMM_PLUS_TIMES>
 __global__ void __launch_bounds__(LANE_WARPS * 32)
 k_lane_rows(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri, const DevStats* st,
             int bin_lo, int bin_hi, int32_t* __restrict__ c_cnt, const int32_t* __restrict__ c_rp,
@@ -111,7 +112,7 @@ k_lane_rows(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
             if (fresh) ++nd;
             if (NUM) {
               T* vp = &vals[h * 32 + lane];
-              *vp = fresh ? a * bb[u] : fma(a, bb[u], *vp);
+              *vp = fresh ? SrOps<T, SR>::mul(a, bb[u]) : SrOps<T, SR>::madd(a, bb[u], *vp);
             }
           }
         }
@@ -168,11 +169,11 @@ constexpr size_t lane_rows_smem() {
 }
 
 // Launch over the rows of bins [lo, hi] (rows: their number, -1 unknown).
-template <bool NUM, typename T>
+template <bool NUM, typename T, int SR = SPGEMM_PLUS_TIMES>
 static cudaError_t lane_rows(const LaunchCtx& c, const Csr& A, const Csr& B, const T* av, const T* bv,
                              const RowInfo& ri, int lo, int hi, int32_t* c_cnt, const int32_t* c_rp,
                              int32_t* c_ci, T* c_v, long long rows) {
-  auto k = k_lane_rows<NUM, T>;
+  auto k = k_lane_rows<NUM, T, SR>;
   const size_t smem = lane_rows_smem<NUM, T>();
   const int occ = kernel_blocks_per_sm(k, LANE_WARPS * 32, smem);
   if (occ <= 0) return cudaErrorInvalidConfiguration;

@@ -23,6 +23,7 @@
 #pragma once
 
 #include "internal.cuh"
+#include "semiring.cuh"
 
 namespace sg {
 
@@ -32,7 +33,7 @@ namespace sg {
 // so every slot is a run of G consecutive elements after the sort; the
 // bitonic network exchanges through shuffles (partner distance < G) or
 // between a lane's own slots (distance >= G).
-template <int G, int E, bool NUM, typename T>
+template <int G, int E, bool NUM, typename T, int SR = SPGEMM_PLUS_TIMES>
 __global__ void __launch_bounds__(256)
 k_tiny(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo ri,
        const DevStats* st, int bin_lo, int bin_hi, int32_t* __restrict__ c_cnt,
@@ -100,7 +101,7 @@ k_tiny(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo
         if (q >= 0 && q < tot) {
           const int bi = os + q - oex;
           col[s] = B.ci[bi];
-          if (NUM) val[s] = oa * bv[bi];
+          if (NUM) val[s] = SrOps<T, SR>::mul(oa, bv[bi]);
         }
       }
       done += tot;
@@ -175,13 +176,13 @@ k_tiny(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, RowInfo
       for (int d = 1; d < G; d <<= 1) {
         const T t = __shfl_down_sync(FULL, a, d, G);
         const int tc = __shfl_down_sync(FULL, col[s], d, G);
-        if (gl + d < G && tc == col[s]) a += t;
+        if (gl + d < G && tc == col[s]) a = SrOps<T, SR>::add(a, t);
       }
       if (s < E - 1) {
         const int lastc = __shfl_sync(FULL, col[s], G - 1, G);
         const int nextc = __shfl_sync(FULL, col[s < E - 1 ? s + 1 : s], 0, G);
         const T nexta = __shfl_sync(FULL, acc[s < E - 1 ? s + 1 : s], 0, G);
-        if (nextc == lastc && col[s] == lastc) a += nexta;
+        if (nextc == lastc && col[s] == lastc) a = SrOps<T, SR>::add(a, nexta);
       }
       acc[s] = a;
     }

@@ -1,5 +1,7 @@
-"""GPU parity of the semiring masked product (``spgemm_semiring``:
-min-plus, max-plus, or-and) against the CPU oracle, through the C ABI.
+"""GPU parity of the semiring products against the CPU oracle, through the
+C ABI: the masked product (``spgemm_semiring``: min-plus, max-plus, or-and)
+and the full product whose numeric pass accumulates over the semiring (the
+plan option ``semiring``).
 Min and max do not depend on the order of the sums, so every value is
 compared bit for bit; FP32 results equal the oracle's FP64 result rounded to
 FP32 (rounding is monotone, and the sums of FP32 inputs are exact in FP64).
@@ -70,6 +72,69 @@ def test_semiring_long_mask_rows_and_full_pattern(api, oracle_mod, semiring):
     R = oracle_mod.spgemm(A, B)
     assert np.array_equal(C.col_idx.cpu().numpy(), R.col_idx)
     assert np.array_equal(C.vals.cpu().numpy(), oracle_mod.masked_semiring(A, B, R, semiring))
+
+
+@pytest.mark.parametrize("semiring", SEMIRINGS)
+def test_semiring_product_every_path(api, oracle_mod, semiring):
+    """R-MAT scale 14 A*A through the numeric pass's own semiring
+    accumulators: rows of at most 16 products in the register sort, up to 128
+    in the warp hash table, up to 65,536 in the warp window, 102 rows above
+    that in the block window.
+    Structure equal to A*A's, every value exact against the oracle."""
+    A = gen.rmat(14, 16)
+    dA = api.DeviceCSR.from_host(A)
+    C = api.spgemm_semiring(dA, dA, semiring)
+    torch.cuda.synchronize()
+    R = oracle_mod.spgemm(A, A)
+    assert np.array_equal(C.row_ptr.cpu().numpy(), R.row_ptr)
+    assert np.array_equal(C.col_idx.cpu().numpy(), R.col_idx)
+    assert np.array_equal(C.vals.cpu().numpy(), oracle_mod.masked_semiring(A, A, R, semiring))
+
+
+@pytest.mark.parametrize("semiring", SEMIRINGS)
+def test_semiring_product_stencil_lane_rows(api, oracle_mod, semiring):
+    """3D 7-point Laplacian 20^3 squared: every row has at most 49 products,
+    so the numeric pass takes the lane-per-row tables (and the register sort
+    for boundary rows of at most 16)."""
+    A = gen.laplacian_3d(20)
+    dA = api.DeviceCSR.from_host(A)
+    C = api.spgemm_semiring(dA, dA, semiring)
+    torch.cuda.synchronize()
+    R = oracle_mod.spgemm(A, A)
+    assert np.array_equal(C.col_idx.cpu().numpy(), R.col_idx)
+    assert np.array_equal(C.vals.cpu().numpy(), oracle_mod.masked_semiring(A, A, R, semiring))
+
+
+@pytest.mark.parametrize("semiring", SEMIRINGS)
+@pytest.mark.parametrize("force_path", [3, 4])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_semiring_product_forced_paths(api, oracle_mod, semiring, force_path, dtype):
+    """Every non-empty row through the warp window (3) or the block window
+    (4), rectangular with empty rows, in FP64 and FP32 (FP32 inputs whose
+    sums are exact, so the result is the oracle's rounded to FP32)."""
+    A = gen.random_csr(400, 300, 0.04, 11, empty_rows=0.1).astype(np.float32).astype(np.float64)
+    B = gen.random_csr(300, 3000, 0.02, 12, empty_rows=0.1).astype(np.float32).astype(np.float64)
+    dA = api.DeviceCSR.from_host(A, dtype=dtype)
+    dB = api.DeviceCSR.from_host(B, dtype=dtype)
+    C = api.spgemm_semiring(dA, dB, semiring, force_path=force_path)
+    torch.cuda.synchronize()
+    R = oracle_mod.spgemm(A, B)
+    assert np.array_equal(C.col_idx.cpu().numpy(), R.col_idx)
+    ref = oracle_mod.masked_semiring(A, B, R, semiring)
+    if dtype == torch.float32:
+        ref = ref.astype(np.float32)
+    assert np.array_equal(C.vals.cpu().numpy(), ref)
+
+
+def test_semiring_plan_rejects_backward_and_unknown(api):
+    from paper_2112_10037_gb300 import _native as nat
+    A = api.DeviceCSR.from_host(gen.random_csr(20, 20, 0.2, 1))
+    with pytest.raises(nat.SpgemmError) as ei:
+        api.Plan(A, A, semiring="min_plus", backward=True)
+    assert ei.value.status == 1
+    with pytest.raises(nat.SpgemmError) as ei:
+        api.Plan(A, A, semiring=7)
+    assert ei.value.status == 1
 
 
 def test_min_plus_all_pairs_shortest_paths(api):
