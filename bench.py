@@ -743,6 +743,48 @@ def run_backward(args):
     return out
 
 
+def run_transpose(args):
+    """The CSR transpose (stable radix scatter on the column index) of two
+    products' C: R-MAT scale 16 A*A (164 M entries, 65,536 columns: two
+    9-bit digit passes) and the 3D stencil 96^3 A*A (21.7 M entries, 884,736
+    columns: three passes), with FP64 values and source positions, and of
+    the structure alone.  GB/s counts the algorithmic bytes: M's column
+    indices and values read once, M^T's column indices, values and source
+    positions written once, and both row pointers.  Inputs larger than L2."""
+    import torch
+    from paper_2112_10037_gb300 import api, build as bld
+    bld.build()
+    stream = torch.cuda.current_stream()
+    peak, peak_kind = measured_hbm_peak()
+    res = {}
+    for name, M in (("rmat_s16_AxA", gen.rmat(16, 16)), ("laplacian3d_96_AxA", gen.laplacian_3d(96))):
+        dM = api.DeviceCSR.from_host(M)
+        C = api.spgemm(dM, dM)
+        S = api.DeviceCSR(C.nrows, C.ncols, C.row_ptr, C.col_idx, None)
+        del dM
+        torch.cuda.synchronize()
+        nnz, rows, cols = C.nnz, C.nrows, C.ncols
+        entry = {"nnz": nnz, "nrows": rows, "ncols": cols}
+        for kind, M_, want_src, vb in (("values_and_src", C, True, 8), ("structure", S, False, 0)):
+            for _ in range(args.warmup):
+                api.transpose(M_, want_src=want_src)
+            ms, _ = _events_ms(lambda: api.transpose(M_, want_src=want_src), args.steps, stream)
+            nbytes = nnz * (4 + vb) + 4 * (rows + 1) + nnz * (4 + vb + (4 if want_src else 0)) + 4 * (cols + 1)
+            gbs = nbytes / (ms / 1e3) / 1e9
+            entry[kind] = {"ms": round(ms, 4), "algorithmic_bytes": int(nbytes), "gbs": round(gbs, 1),
+                           "hbm_frac": round(gbs / peak, 4)}
+        res[name] = entry
+        del C, S
+        torch.cuda.empty_cache()
+    first = res["rmat_s16_AxA"]["values_and_src"]
+    out = _base_line("CSR transpose GB/s (algorithmic bytes)", first["gbs"], "GB/s", args, first["ms"],
+                     {"workload": "transpose_rmat_s16_AxA_and_laplacian3d_96_AxA", "l2": "inputs larger than L2"})
+    out["roofline"] = {"bound": "hbm", "achieved": first["gbs"], "peak": peak, "unit": "GB/s",
+                       "frac": first["hbm_frac"], "peak_kind": peak_kind + " hbm_gbs (copy)", "traffic": None}
+    out["matrices"] = res
+    return out
+
+
 def run_triangles(args):
     """Masked product (L*L) .* L on the strictly lower triangle L of the
     undirected R-MAT graph (scale --rmat-scale, edge factor 16): the sum of
@@ -1103,7 +1145,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat",
                     choices=["rmat", "lap2d", "stencil3d", "batched", "galerkin", "backward", "triangles", "omar",
-                             "variants", "stencil_device", "sharing"])
+                             "variants", "stencil_device", "sharing", "transpose"])
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-scale", type=float, default=1.0,
                     help="row-count scale of the batched instances (1.0 = rows in [1024, 200000])")
@@ -1134,11 +1176,12 @@ def main():
         print(json.dumps(run_reference(args, A, B, desc)), flush=True)
         return
     if args.workload in ("batched", "galerkin", "backward", "triangles", "omar", "variants", "stencil_device",
-                         "sharing"):
+                         "sharing", "transpose"):
         if rank == 0:
             runner = {"batched": run_batched, "galerkin": run_galerkin, "backward": run_backward,
                       "triangles": run_triangles, "omar": run_omar, "variants": run_variants,
-                      "stencil_device": run_stencil_device, "sharing": run_sharing}[args.workload]
+                      "stencil_device": run_stencil_device, "sharing": run_sharing,
+                      "transpose": run_transpose}[args.workload]
             print(json.dumps(runner(args)), flush=True)
         return
     if world > 1:
