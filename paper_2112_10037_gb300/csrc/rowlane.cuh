@@ -174,7 +174,9 @@ k_lane_rows(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, Ro
 // column, then merges them -- the next output column is the smallest head column, its
 // value the products of the heads that hold it, each head advanced past it
 // -- so the row comes out in column order with no table and no ranking.  The
-// sums run in A's order (the first product rounded, later ones fused).
+// sums run in A's order, every product fused into the running sum from the
+// semiring's identity (for plus-times the first product is a*b rounded,
+// +0 where that product is exactly -0).
 // (Measured on the 96^3 stencil: staging only the columns, for more warps
 // per SM, and reading B's values from global memory was 13 % slower; one
 // product per inner round, to issue fewer FP64 warp instructions, 14 %.)
@@ -259,7 +261,7 @@ k_lane_merge(Csr A, Csr B, const T* __restrict__ av, const T* __restrict__ bv, R
       for (int k = 0; k < K; ++k) {
         if (hc[k] == m) {
           const T b = sval[hs[k] * 32 + lane];
-          acc = any ? Ops::madd(a[k], b, acc) : Ops::mul(a[k], b);
+          acc = Ops::madd(a[k], b, any ? acc : Ops::zero());  // one FP64 instruction per head test
           any = true;
           ++hs[k];
           hc[k] = hs[k] < he[k] ? scol[hs[k] * 32 + lane] : INT_MAX;
