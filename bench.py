@@ -414,8 +414,8 @@ def fp64_peak_gflops(torch, dev):
 
 # Sources of the numeric pass's kernels: numeric.cu and everything it
 # includes.  A DRAM-traffic record stays valid while these are unchanged.
-NUMERIC_SOURCES = ["numeric.cu", "launch_util.cuh", "internal.cuh", "numblock.cuh", "numrank.cuh", "numwarp.cuh",
-                   "rowhash.cuh", "rowlane.cuh", "rowpass.cuh", "segstream.cuh"]
+NUMERIC_SOURCES = ["numeric.cu", "numdispatch.cuh", "semiring.cuh", "launch_util.cuh", "internal.cuh", "numblock.cuh",
+                   "numrank.cuh", "numwarp.cuh", "rowhash.cuh", "rowlane.cuh", "rowpass.cuh", "segstream.cuh"]
 
 
 def numeric_digest() -> str:
