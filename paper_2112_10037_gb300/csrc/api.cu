@@ -310,6 +310,20 @@ spgemm_status read_stats(spgemm_plan* p, cudaStream_t s) {
 
 }  // namespace
 
+// Other semirings than plus-times skip the rank-compacted accumulator,
+// register sorts above 128 products, split rows and the non-default window
+// sizes: their options are reset here, for the workspace size and the plan
+// alike.
+static void semiring_defaults(spgemm_opts* o) {
+  if (o->semiring == SPGEMM_PLUS_TIMES) return;
+  o->sort_max = 0;
+  o->rank_min = -1;
+  o->split_min = -1;
+  o->window_warp = 0;
+  o->window_block = 0;
+  o->block_warps = 0;
+}
+
 // base: another plan of the same product whose window-run lists of B this
 // plan reads instead of building its own (null: build them).
 static spgemm_status analyse_impl(const spgemm_csr* A, const spgemm_csr* B, const spgemm_opts* opts,
@@ -326,17 +340,8 @@ static spgemm_status analyse_impl(const spgemm_csr* A, const spgemm_csr* B, cons
   if (o.dtype != SPGEMM_F64 && o.dtype != SPGEMM_F32) return SPGEMM_ERR_INVALID_ARG;
   if (o.force_path < -1 || o.force_path > 4) return SPGEMM_ERR_INVALID_ARG;
   if (o.semiring < SPGEMM_PLUS_TIMES || o.semiring > SPGEMM_OR_AND) return SPGEMM_ERR_INVALID_ARG;
-  if (o.semiring != SPGEMM_PLUS_TIMES) {
-    // other semirings skip the rank-compacted accumulator, register sorts
-    // above 128 products, split rows and the non-default window sizes
-    if (o.backward) return SPGEMM_ERR_INVALID_ARG;
-    o.sort_max = 0;
-    o.rank_min = -1;
-    o.split_min = -1;
-    o.window_warp = 0;
-    o.window_block = 0;
-    o.block_warps = 0;
-  }
+  if (o.semiring != SPGEMM_PLUS_TIMES && o.backward) return SPGEMM_ERR_INVALID_ARG;
+  semiring_defaults(&o);
   const long long rb = o.row_begin, re = o.row_end < 0 ? A->nrows : o.row_end;
   if (rb < 0 || re < rb || re > A->nrows) return SPGEMM_ERR_DIM_MISMATCH;
   const Layout L = layout_for(o, re - rb, A->nnz, B->nrows, B->ncols, B->nnz, base == nullptr);
@@ -469,6 +474,7 @@ spgemm_status spgemm_workspace_size(const spgemm_csr* A, const spgemm_csr* B, co
   if ((s = check_csr(B)) != SPGEMM_OK) return s;
   spgemm_opts o;
   if (opts) o = *opts; else spgemm_opts_default(&o);
+  semiring_defaults(&o);  // the options spgemm_analyse will use
   const long long rb = o.row_begin, re = o.row_end < 0 ? A->nrows : o.row_end;
   if (rb < 0 || re < rb || re > A->nrows) return SPGEMM_ERR_DIM_MISMATCH;
   *bytes = layout_for(o, re - rb, A->nnz, B->nrows, B->ncols, B->nnz).total;

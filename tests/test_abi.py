@@ -211,3 +211,43 @@ def test_host_product_host_checks_without_gpu(libpath):
         nat.spgemm_host_product_finish(0, 1 << 20, 1 << 21, 1 << 22, 1 << 23, 1 << 20, 0, 0)
     assert ei.value.status == 1
     nat.spgemm_host_product_destroy(0)
+
+
+def test_semiring_option_host_checks_without_gpu(libpath):
+    """The plan option `semiring` is checked on the host before any device
+    work: an unknown semiring, or a semiring plan that also asks for the
+    backward pass, is refused."""
+    A = nat.spgemm_csr()
+    A.nrows, A.ncols, A.nnz = 10, 20, 0
+    A.row_ptr = 16
+    B = nat.spgemm_csr()
+    B.nrows, B.ncols, B.nnz = 20, 5, 0
+    B.row_ptr = 16
+    o = nat.spgemm_opts_default()
+    assert o.semiring == nat.SPGEMM_PLUS_TIMES
+    for bad in (-1, 4, 7):
+        o.semiring = bad
+        with pytest.raises(nat.SpgemmError) as ei:
+            nat.spgemm_analyse(A, B, o, 256, 1 << 20, 0)
+        assert ei.value.status == 1
+    o.semiring = nat.SPGEMM_MIN_PLUS
+    o.backward = 1
+    with pytest.raises(nat.SpgemmError) as ei:
+        nat.spgemm_analyse(A, B, o, 256, 1 << 20, 0)
+    assert ei.value.status == 1
+
+
+def test_semiring_workspace_uses_the_plan_defaults(libpath):
+    """A semiring plan runs at the default window sizes whatever the options
+    say, so its workspace size ignores them as the plan does."""
+    A = nat.spgemm_csr()
+    A.nrows, A.ncols, A.nnz = 1000, 2000, 50000
+    A.row_ptr, A.col_idx = 16, 16
+    B = nat.spgemm_csr()
+    B.nrows, B.ncols, B.nnz = 2000, 3000, 80000
+    B.row_ptr, B.col_idx = 16, 16
+    o = nat.spgemm_opts_default()
+    o.semiring = nat.SPGEMM_MIN_PLUS
+    plain = nat.spgemm_workspace_size(A, B, o)
+    o.window_warp, o.window_block, o.block_warps, o.split_min, o.sort_max = 4096, 2048, 4, 4096, 512
+    assert nat.spgemm_workspace_size(A, B, o) == plain

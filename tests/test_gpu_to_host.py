@@ -161,3 +161,15 @@ def test_host_product_fp32_and_empty(api, oracle_mod):
     F = gen.CSR(40, 30, np.zeros(41, np.int32), np.zeros(0, np.int32), np.zeros(0))
     rp, ci, v = api.spgemm_host(E, F, chunks=4)
     assert rp.numel() == 51 and int(rp.abs().sum()) == 0 and ci.numel() == 0 and v.numel() == 0
+
+
+@pytest.mark.parametrize("semiring", ["min_plus", "or_and"])
+def test_host_product_semiring(api, oracle_mod, semiring):
+    """The host-buffer product with the plan option `semiring`: C's pattern
+    from the symbolic pass, its values over the semiring, exact against the
+    oracle's semiring values on that pattern."""
+    A = gen.rmat(11, 8)
+    rp, ci, v = api.spgemm_host(A, chunks=3, semiring=semiring)
+    R = oracle_mod.spgemm(A, A)
+    assert np.array_equal(rp.numpy(), R.row_ptr) and np.array_equal(ci.numpy(), R.col_idx)
+    assert np.array_equal(v.numpy(), oracle_mod.masked_semiring(A, A, R, semiring))
