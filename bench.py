@@ -1159,7 +1159,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-secondary", action="store_true",
                     help="default workload: skip the short runs of the other workloads")
-    ap.add_argument("--e2e-chunks", type=int, default=4,
+    ap.add_argument("--e2e-chunks", type=int, default=8,
                     help="row ranges of the end-to-end leg (computed while earlier ranges are copied back)")
     ap.add_argument("--e2e-streams", type=int, default=1, help="compute streams of the end-to-end leg")
     ap.add_argument("--e2e-order", default="rows", choices=["products", "rows"],

@@ -366,7 +366,8 @@ spgemm_status spgemm_host_product_workspace_size(const spgemm_csr* A, const spge
 
 /* Copies A and B (host CSR, values of opts->dtype) into the workspace on
  * `stream`, analyses the product, runs the symbolic pass and cuts the rows
- * into at most `chunks` ranges of about equal output.  BLOCKS on `stream` to
+ * into at most `chunks` ranges by output (the last rows' range about
+ * 1/(2 chunks) of nnz(C), the others equal).  BLOCKS on `stream` to
  * return nnz(C).  The workspace (device, 16-byte aligned) must stay valid
  * until spgemm_host_product_destroy; the host inputs may be released on
  * return.  opts: row_begin/row_end, backward and validate are ignored. */
@@ -379,9 +380,10 @@ spgemm_status spgemm_host_product_begin(const spgemm_csr* A, const spgemm_csr* B
 spgemm_status spgemm_host_product_staging_size(const spgemm_host_product* product, size_t* bytes);
 
 /* Numeric pass of every row range on `stream` into the staging buffer
- * (device, 16-byte aligned), each range copied into c_col_idx / c_vals
- * (host, nnz(C) entries) on copy_stream as soon as it is done (NULL:
- * `stream`, no overlap); c_row_ptr (host, nrows(A) + 1 entries) receives C's
+ * (device, 16-byte aligned), from the last range to the first (the small
+ * last-rows range first, so the copies start early), each range copied into
+ * c_col_idx / c_vals (host, nnz(C) entries) on copy_stream as soon as it is
+ * done (NULL: `stream`, no overlap); c_row_ptr (host, nrows(A) + 1 entries) receives C's
  * row pointer.  BLOCKS until C is complete in host memory; reports any
  * device error of the range plans.  Repeatable (the inputs' values are those
  * copied by begin). */

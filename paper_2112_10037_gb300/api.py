@@ -437,8 +437,9 @@ def spgemm_host(A, B=None, dtype=torch.float64, chunks: int = 4, out=None, trace
     """C = A*B from host memory to host memory through the C ABI's
     host-buffer product (``spgemm_host_product_begin`` / ``_finish``): the
     inputs are copied to the device, one symbolic pass sizes C, and the
-    numeric pass runs in ``chunks`` row ranges of about equal output, each
-    copied back while the later ones compute.  A, B: host CSR (``gen.CSR``
+    numeric pass runs in ``chunks`` row ranges cut by output (a small range
+    of the last rows, computed first so the copies start early, then equal
+    ones from the bottom up), each copied back while the next ones compute.  A, B: host CSR (``gen.CSR``
     or objects with nrows / ncols / row_ptr / col_idx / vals as numpy arrays
     or CPU tensors -- pinned memory for overlapped copies -- values already
     of ``dtype``); B defaults to A (copied once).  ``out`` = (row_ptr,

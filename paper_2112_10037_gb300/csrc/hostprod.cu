@@ -145,13 +145,19 @@ spgemm_status spgemm_host_product_begin(const spgemm_csr* A, const spgemm_csr* B
     delete h;
     return SPGEMM_ERR_CUDA;
   }
-  // row ranges of about equal output: range r ends at the first row whose
-  // row pointer reaches r/chunks of nnz(C)
+  // row ranges cut by output.  The copies run back to back once the first
+  // range computed is done, so only that range's numeric pass is not hidden
+  // under a copy: it is the last rows' range, about 1/(2 chunks) of nnz(C)
+  // (the heaviest rows, whose numeric time per output is highest, sit at
+  // the top of a power-law matrix), and finish computes the ranges from the
+  // last to the first.  The other ranges share the rest of C equally; range r
+  // ends at the first row whose row pointer reaches its target.
   const long long m = h->m, total = h->nnz_c;
   const long long nr = std::max(1ll, std::min((long long)chunks, m));
+  const long long last = nr > 1 ? total / (2 * nr) : 0;
   h->bounds.push_back(0);
   for (long long r = 1; r < nr; ++r) {
-    const long long target = total * r / nr;
+    const long long target = (total - last) * r / (nr - 1);
     const long long cut = std::lower_bound(h->host_rp.begin(), h->host_rp.end(), (int32_t)target) - h->host_rp.begin();
     if (cut > h->bounds.back() && cut < m) h->bounds.push_back(cut);
   }
@@ -217,7 +223,8 @@ spgemm_status spgemm_host_product_finish(spgemm_host_product* h, int32_t* c_row_
   if (s != SPGEMM_OK) { cleanup(); return s; }
   cudaError_t e = cudaEventRecord(ev[4 * nr], st);  // origin of the timeline
   if (e == cudaSuccess && cp != st) e = cudaStreamWaitEvent(cp, ev[4 * nr], 0);
-  for (size_t r = 0; r < nr && e == cudaSuccess && s == SPGEMM_OK; ++r) {
+  for (size_t q = 0; q < nr && e == cudaSuccess && s == SPGEMM_OK; ++q) {
+    const size_t r = nr - 1 - q;  // last range first
     const long long rb = h->bounds[r];
     const long long o = h->host_rp[rb], n = (long long)h->host_rp[h->bounds[r + 1]] - o;
     e = cudaEventRecord(ev[4 * r], st);

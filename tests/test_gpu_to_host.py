@@ -105,7 +105,8 @@ def test_adopt_refuses_split_rows(api):
 def test_host_product_rmat_aliased(api, oracle_mod, chunks):
     """Host CSR in, host CSR out through spgemm_host_product_begin/finish,
     B aliased to A (one copy), against the oracle; the device timeline has
-    one numeric and one copy interval per row range, in order."""
+    one numeric and one copy interval per row range, computed and copied
+    from the last range to the first."""
     A = gen.rmat(12, 8)
     tr = {}
     rp, ci, v = api.spgemm_host(A, chunks=chunks, trace=tr)
@@ -119,8 +120,9 @@ def test_host_product_rmat_aliased(api, oracle_mod, chunks):
     for r in range(nr):
         assert d["numeric_start"][r] <= d["numeric_end"][r] <= d["copy_start"][r] + 1e-3
         assert d["copy_start"][r] <= d["copy_end"][r]
-        if r:
-            assert d["numeric_start"][r] >= d["numeric_end"][r - 1] - 1e-3
+        if r + 1 < nr:  # ranges are computed from the last to the first
+            assert d["numeric_start"][r] >= d["numeric_end"][r + 1] - 1e-3
+            assert d["copy_start"][r] >= d["copy_end"][r + 1] - 1e-3
 
 
 def test_host_product_rectangular_pinned_reused(api, oracle_mod):
