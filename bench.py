@@ -999,8 +999,9 @@ def run_secondary(args):
     """The other workloads of the measurement plan, each in a short form, for
     the default bench line: the 3D stencil product, the Galerkin chain replay,
     the differentiation workload's forward and backward passes, triangle
-    counting on the R-MAT scale-18 graph and the 512-instance batched
-    workload at its stated size against one-by-one calls."""
+    counting on the R-MAT scale-18 graph, the 512-instance batched workload
+    at its stated size against one-by-one calls, the transpose of two
+    products' C, and the column-wise and semiring products."""
     import copy
     import torch
     a = copy.copy(args)
@@ -1046,6 +1047,20 @@ def run_secondary(args):
                 "speedup_numeric": r["speedup_numeric"], "waves": r["config"]["waves"],
                 "products": r["config"]["products"], "nnz_C": r["config"]["nnz_C"]}
     keep("batched_512_full_size", bat)
+
+    def tra():
+        r = run_transpose(a)
+        return {name: {"values_and_src": m["values_and_src"], "structure_ms": m["structure"]["ms"]}
+                for name, m in r["matrices"].items()}
+    keep("transpose", tra)
+
+    def var():
+        r = run_variants(a)
+        return {name: {"colwise_ms": m["colwise"]["ms"], "rowwise_ms": m["rowwise"]["ms"],
+                       "min_plus_ms": m["min_plus"]["ms"], "min_plus_numeric_ms": m["min_plus"]["numeric_ms"],
+                       "min_plus_masked_ms": m["min_plus"]["masked_ms"], "or_and_ms": m["or_and"]["ms"]}
+                for name, m in r["matrices"].items()}
+    keep("column_wise_and_semiring", var)
     return out
 
 
