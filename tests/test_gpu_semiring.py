@@ -75,20 +75,24 @@ def test_semiring_long_mask_rows_and_full_pattern(api, oracle_mod, semiring):
 
 
 @pytest.mark.parametrize("semiring", SEMIRINGS)
-def test_semiring_product_every_path(api, oracle_mod, semiring):
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_semiring_product_every_path(api, oracle_mod, semiring, dtype):
     """R-MAT scale 14 A*A through the numeric pass's own semiring
     accumulators: rows of at most 16 products in the register sort, up to 128
     in the warp hash table, up to 65,536 in the warp window, 102 rows above
     that in the block window.
-    Structure equal to A*A's, every value exact against the oracle."""
-    A = gen.rmat(14, 16)
-    dA = api.DeviceCSR.from_host(A)
+    Structure equal to A*A's, every value exact against the oracle (FP32:
+    inputs exact in FP32, the oracle's FP64 values rounded to FP32, since
+    one rounding of a + b commutes with min and max)."""
+    A = gen.rmat(14, 16).astype(np.float32).astype(np.float64)
+    dA = api.DeviceCSR.from_host(A, dtype=dtype)
     C = api.spgemm_semiring(dA, dA, semiring)
     torch.cuda.synchronize()
     R = oracle_mod.spgemm(A, A)
     assert np.array_equal(C.row_ptr.cpu().numpy(), R.row_ptr)
     assert np.array_equal(C.col_idx.cpu().numpy(), R.col_idx)
-    assert np.array_equal(C.vals.cpu().numpy(), oracle_mod.masked_semiring(A, A, R, semiring))
+    ref = oracle_mod.masked_semiring(A, A, R, semiring)
+    assert np.array_equal(C.vals.cpu().numpy(), ref.astype(np.float32) if dtype == torch.float32 else ref)
 
 
 @pytest.mark.parametrize("semiring", SEMIRINGS)
