@@ -50,6 +50,35 @@ class DeviceCSR:
         return CSR(self.nrows, self.ncols, self.row_ptr.cpu().numpy().astype(np.int32),
                    self.col_idx.cpu().numpy(), vals)
 
+    @staticmethod
+    def from_torch(t: torch.Tensor) -> "DeviceCSR":
+        """From a ``torch.sparse_csr_tensor`` (its index tensors converted to
+        int32; the values are used as they are)."""
+        if not isinstance(t, torch.Tensor) or t.layout != torch.sparse_csr:
+            raise TypeError("expected a torch.sparse_csr_tensor")
+        if t.dim() != 2:
+            raise ValueError("expected a 2-D sparse CSR tensor")
+        rp = t.crow_indices().to(torch.int32).contiguous()
+        ci = t.col_indices().to(torch.int32).contiguous()
+        return DeviceCSR(int(t.shape[0]), int(t.shape[1]), rp, ci, t.values().contiguous())
+
+    @staticmethod
+    def from_tuple(parts) -> "DeviceCSR":
+        """From (indptr, indices, values, (nrows, ncols)) tensors."""
+        indptr, indices, values, shape = parts
+        return DeviceCSR(int(shape[0]), int(shape[1]), indptr.to(torch.int32).contiguous(),
+                         indices.to(torch.int32).contiguous(), values.contiguous() if values is not None else None)
+
+    def to_torch(self) -> torch.Tensor:
+        """As a ``torch.sparse_csr_tensor`` sharing this matrix's tensors."""
+        vals = self.vals if self.vals is not None else torch.ones(self.nnz, dtype=torch.float64,
+                                                                  device=self.row_ptr.device)
+        return torch.sparse_csr_tensor(self.row_ptr, self.col_idx, vals, size=(self.nrows, self.ncols))
+
+    def to_tuple(self):
+        """(indptr, indices, values, (nrows, ncols))."""
+        return self.row_ptr, self.col_idx, self.vals, (self.nrows, self.ncols)
+
     def c_struct(self) -> nat.spgemm_csr:
         s = nat.spgemm_csr()
         s.nrows, s.ncols, s.nnz = self.nrows, self.ncols, self.nnz
@@ -181,14 +210,52 @@ class Plan:
             pass
 
 
-def spgemm(A: DeviceCSR, B: DeviceCSR, dtype=None, **opt_kw) -> DeviceCSR:
-    """C = A*B on the device (analyse, symbolic, numeric)."""
+def _as_csr(M):
+    """(DeviceCSR, kind) for a DeviceCSR, a torch.sparse_csr_tensor or an
+    (indptr, indices, values, shape) tuple."""
+    if isinstance(M, DeviceCSR):
+        return M, "csr"
+    if isinstance(M, torch.Tensor):
+        return DeviceCSR.from_torch(M), "torch"
+    if isinstance(M, (tuple, list)) and len(M) == 4:
+        return DeviceCSR.from_tuple(M), "tuple"
+    raise TypeError("expected DeviceCSR, torch.sparse_csr_tensor or (indptr, indices, values, shape)")
+
+
+def _as_kind(C: DeviceCSR, kind):
+    return C.to_torch() if kind == "torch" else (C.to_tuple() if kind == "tuple" else C)
+
+
+def spgemm(A, B, dtype=None, **opt_kw):
+    """C = A*B on the device (analyse, symbolic, numeric).  A and B are
+    DeviceCSR, ``torch.sparse_csr_tensor`` (indices converted to int32) or
+    (indptr, indices, values, shape) tuples on the device; C comes back in
+    A's form."""
+    A, kind = _as_csr(A)
+    B, _ = _as_csr(B)
     dtype = dtype or (A.vals.dtype if A.vals is not None else torch.float64)
     plan = Plan(A, B, dtype=dtype, **opt_kw)
     rp, nnz = plan.symbolic()
     ci, v = plan.numeric(A.vals, B.vals)
     plan.close()
-    return DeviceCSR(plan.nrows, B.ncols, rp, ci, v)
+    return _as_kind(DeviceCSR(plan.nrows, B.ncols, rp, ci, v), kind)
+
+
+def batched(pairs, dtype=torch.float64, **opt_kw):
+    """C_i = A_i * B_i for every pair through one ``Batch`` (stacked
+    launches, waves as needed); returns the list of C_i as DeviceCSR."""
+    b = Batch([(_as_csr(a)[0], _as_csr(bb)[0]) for a, bb in pairs], dtype=dtype, **opt_kw)
+    b.symbolic()
+    b.numeric()
+    return b.results()
+
+
+def galerkin(P, A, dtype=torch.float64, **opt_kw):
+    """The coarse operator P^T (A P) (``Galerkin``, one call); returned in
+    A's form."""
+    P_, _ = _as_csr(P)
+    A_, kind = _as_csr(A)
+    return _as_kind(Galerkin(P_, A_, dtype=dtype, **opt_kw).Ac, kind)
 
 
 def spgemm_colwise(A: DeviceCSR, B: DeviceCSR, dtype=None, **opt_kw) -> DeviceCSR:

@@ -419,3 +419,52 @@ def test_hash_path_galerkin_small(api, oracle_mod):
     assert_structure_equal(G, R)
     assert_values_exact(G.vals, R.vals)
     assert stats[2][1] > 0
+
+
+def test_torch_sparse_and_tuple_inputs(api, oracle_mod):
+    """spgemm on torch.sparse_csr_tensor inputs (int64 indices) returns a
+    torch.sparse_csr_tensor, on (indptr, indices, values, shape) tuples a
+    tuple; both equal the oracle's product."""
+    A = gen.random_csr(300, 200, 0.05, 21, values="int")
+    B = gen.random_csr(200, 250, 0.05, 22, values="int")
+    R = oracle_mod.spgemm(A, B)
+    dev = torch.device("cuda")
+    ta = torch.sparse_csr_tensor(torch.from_numpy(A.row_ptr.astype(np.int64)),
+                                 torch.from_numpy(A.col_idx.astype(np.int64)),
+                                 torch.from_numpy(A.vals), size=(A.nrows, A.ncols)).to(dev)
+    tb = torch.sparse_csr_tensor(torch.from_numpy(B.row_ptr.astype(np.int64)),
+                                 torch.from_numpy(B.col_idx.astype(np.int64)),
+                                 torch.from_numpy(B.vals), size=(B.nrows, B.ncols)).to(dev)
+    tc = api.spgemm(ta, tb)
+    assert tc.layout == torch.sparse_csr and tuple(tc.shape) == (300, 250)
+    assert np.array_equal(tc.crow_indices().cpu().numpy(), R.row_ptr)
+    assert np.array_equal(tc.col_indices().cpu().numpy(), R.col_idx)
+    assert np.array_equal(tc.values().cpu().numpy(), R.vals)
+    dA, dB = api.DeviceCSR.from_host(A), api.DeviceCSR.from_host(B)
+    rp, ci, v, shape = api.spgemm(dA.to_tuple(), dB.to_tuple())
+    assert shape == (300, 250) and np.array_equal(ci.cpu().numpy(), R.col_idx)
+    assert np.array_equal(v.cpu().numpy(), R.vals)
+
+
+def test_batched_and_galerkin_helpers(api, oracle_mod):
+    """The one-call helpers: batched() over three pairs and galerkin(P, A)
+    against the oracle (integer values: exact)."""
+    rng = np.random.default_rng(5)
+    pairs, refs = [], []
+    for s in range(3):
+        A = gen.random_rows(60 + 10 * s, 50, rng.integers(0, 8, size=60 + 10 * s), rng, values="int")
+        B = gen.random_rows(50, 80, rng.integers(0, 8, size=50), rng, values="int")
+        pairs.append((api.DeviceCSR.from_host(A), api.DeviceCSR.from_host(B)))
+        refs.append(oracle_mod.spgemm(A, B))
+    for C, R in zip(api.batched(pairs), refs):
+        assert np.array_equal(C.row_ptr.cpu().numpy(), R.row_ptr)
+        assert np.array_equal(C.col_idx.cpu().numpy(), R.col_idx)
+        assert np.array_equal(C.vals.cpu().numpy(), R.vals)
+    A = gen.laplacian_2d(16)
+    n = A.nrows
+    P = gen.CSR(n, n // 4, np.arange(n + 1, dtype=np.int32), (np.arange(n) // 4).astype(np.int32), np.ones(n))
+    Ac = api.galerkin(api.DeviceCSR.from_host(P), api.DeviceCSR.from_host(A))
+    Pt = oracle_mod.transpose(P)
+    R = oracle_mod.spgemm(Pt, oracle_mod.spgemm(A, P))
+    assert np.array_equal(Ac.col_idx.cpu().numpy(), R.col_idx)
+    assert np.array_equal(Ac.vals.cpu().numpy(), R.vals)
